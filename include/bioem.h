@@ -1,0 +1,156 @@
+/*
+ * bioem.h — C ABI of a GB300 (sm_103a) implementation of the BioEM scoring hot path:
+ * the posterior of every particle image given a structural model, integrated over
+ * orientations x PSFs x in-plane displacements (Cossio, Rohr et al., "BioEM: GPU-accelerated
+ * computing of Bayesian inference of electron microscopy images", arXiv:1609.06634).
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named d_* are DEVICE pointers on the context's device, owned by the caller;
+ *     the library never frees them and keeps no reference to them after the call returns.
+ *     Host pointers are named without the prefix.
+ *   - Images are float32, row-major [n][ny][nx] (x fastest); pixel (j, k) is at
+ *     x_j = (j - nx/2) * pixel_A, y_k = (k - ny/2) * pixel_A (Eq. 1's pixel positions).
+ *     Only square images with nx = ny in {32, 64, 128} are supported in this version.
+ *   - Handles (bioem_ctx, bioem_images, bioem_projset) are owned by the library and freed by
+ *     the matching bioem_free_* / bioem_destroy call.
+ *   - Work is enqueued asynchronously on the context's CUDA stream (the caller's stream; not
+ *     owned).  Errors detectable on the host are returned immediately; errors found by kernels
+ *     (a numerically degenerate image or projection) are recorded in a device status word that
+ *     bioem_get_status() reads after synchronising the stream.
+ *   - Return value: BIOEM_OK (0) or a negative BIOEM_ERR_* code.  Outputs are written only when
+ *     the call (and, for device-detected errors, the stream) completes without error.
+ *   - No C++ exception crosses this interface.
+ */
+#ifndef BIOEM_H
+#define BIOEM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BIOEM_OK 0
+#define BIOEM_ERR_INVALID_ARG (-1)      /* null pointer, negative count, mismatched handles      */
+#define BIOEM_ERR_UNSUPPORTED_SIZE (-2) /* image size or shift window this build does not handle */
+#define BIOEM_ERR_OOM (-3)              /* device allocation failed                              */
+#define BIOEM_ERR_CUDA (-4)             /* a CUDA runtime call or kernel launch failed           */
+#define BIOEM_ERR_TIMEOUT (-5)          /* a bounded device wait gave up                         */
+#define BIOEM_ERR_NUMERIC (-6)          /* degenerate moments (zero variance) or |rho| >= 1      */
+
+typedef struct bioem_ctx bioem_ctx;
+typedef struct bioem_images bioem_images;
+typedef struct bioem_projset bioem_projset;
+
+/* One point of the PSF grid, in physical units (the CTF and envelope after Eq. 4).
+ * Converted to the paper's coefficients as a = lambda_e * defocus_A / (2 pi),
+ * A = amp_contrast, b = bfactor_A2 / (8 pi^2), lambda_e the relativistic electron wavelength
+ * at voltage_kV; the defocus phase is then pi lambda_e defocus k^2 and the envelope
+ * exp(-B k^2 / 4) for spatial frequency k (1/A).  No spherical aberration term. */
+typedef struct {
+    double defocus_A;
+    double amp_contrast; /* in [0, 1] */
+    double bfactor_A2;   /* >= 0 */
+    double voltage_kV;   /* > 0 */
+} bioem_ctf;
+
+/* Create a context on CUDA device `device`, enqueueing work on `cuda_stream` (a cudaStream_t,
+ * or NULL for the legacy default stream).  Allocates the device status word and uploads the
+ * transform twiddle tables.  *out is set only on success. */
+int bioem_create(bioem_ctx** out, int device, void* cuda_stream);
+
+/* Change the stream later calls enqueue on. */
+int bioem_set_stream(bioem_ctx* ctx, void* cuda_stream);
+
+/* Upper bound (bytes) on the per-pair record buffer bioem_score uses; larger parameter sets
+ * are processed in waves that fit.  Default 2 GiB. */
+int bioem_set_scratch_limit(bioem_ctx* ctx, unsigned long long bytes);
+
+/* Free the context and everything it owns (not the handles made with it). */
+void bioem_destroy(bioem_ctx* ctx);
+
+/* Read and clear the device status word: synchronises the context's stream, writes 0 or a
+ * BIOEM_ERR_* code to *out_status, and returns BIOEM_OK unless the synchronisation failed. */
+int bioem_get_status(bioem_ctx* ctx, int* out_status);
+
+/* Message of the last host-side error of this context (static storage, never NULL). */
+const char* bioem_last_error(const bioem_ctx* ctx);
+const char* bioem_status_string(int status);
+
+/* Image preparation (Sec. 3: the per-image constants C_o, C_oo precomputed once; Sec. 3.3:
+ * the observed images' Fourier transforms precomputed once, C_oo by Plancherel's theorem).
+ *   d_images [n_img][ny][nx] float32, device.  pixel_A > 0.
+ * Computes, per image, the float64 moments C_o = sum o, C_oo = sum o^2, A = n C_oo - C_o^2 and
+ * the zero-mean, unit-norm half spectrum used by bioem_score.  *out is a library-owned handle.
+ * Errors: INVALID_ARG, UNSUPPORTED_SIZE, OOM, CUDA; a zero-variance image sets NUMERIC in the
+ * device status word. */
+int bioem_prepare_images(bioem_ctx* ctx, const float* d_images, int n_img, int nx, int ny,
+                         double pixel_A, bioem_images** out);
+
+/* Calculated images of a model for every parameter set (Fig. 1: rotate, project, PSF; Eqs. 1,
+ * 4, 5).  Parameter set p = iq * nctf + ictf.
+ *   d_atoms [n_atoms][4] float32 device: x, y, z (A) and weight of isotropic Gaussian atoms of
+ *           standard deviation sigma_A; the projection integrates each atom over z and over each
+ *           pixel exactly (erf differences), all atoms, no cutoff, mass outside the box cropped.
+ *   d_quats [nq][4] float32 device: quaternions (w, x, y, z); normalised by the library; active
+ *           rotation r' = R(q) r, then projection along z'.
+ *   ctfs    [nctf] HOST array of PSF grid points.
+ * Stores, per parameter set, the PSF-filtered projection's unit-norm half spectrum and the
+ * float64 moment B = n C_cc - C_c^2.  Memory: nq * nctf * ny * (nx/2 + 1) * 8 bytes.
+ * Errors: INVALID_ARG, UNSUPPORTED_SIZE, OOM, CUDA; an all-zero projection sets NUMERIC. */
+int bioem_project_model(bioem_ctx* ctx, const float* d_atoms, int n_atoms, double sigma_A,
+                        const float* d_quats, int nq, const bioem_ctf* ctfs, int nctf,
+                        int nx, int ny, double pixel_A, bioem_projset** out);
+
+/* Posterior of every image (Eq. 9 as a Riemann sum over the grid, uniform weights):
+ *   d_logP[w] = ln( (1 / (n_ps S)) sum_{p, d} L(w | p, d) ),
+ * with L the likelihood of Eq. 8 integrated in closed form over the normalisation N (real line),
+ * the offset mu (real line) and the noise lambda (0, inf) under flat unit priors:
+ *   ln L = (3-n)/2 ln(A B - X^2) + (n-4)/2 ln B + c(n),   X(d) = n C_co(d) - C_o C_c,
+ *   c(n) = -ln 2 + (1 - n/2) ln 2 pi + ln Gamma((n-3)/2) + (n-3)/2 ln(2n),
+ * C_co(d) = sum_r o(r) I1((r + d) mod N) the cyclic correlation (Sec. 3.3, Eqs. 11-12) for every
+ * displacement d = (dx, dy) with |dx|, |dy| <= max_shift, S = (2 max_shift + 1)^2.
+ *   d_logP            [n_img] float64 device, required.
+ *   d_logP_per_orient [n_img][nq] float64 device or NULL: ln of the mean over (ctf, d) of L for
+ *                     each orientation (Sec. 3.8, posterior as a function of orientation).
+ * Requires images and projset with the same nx, ny, pixel_A; 0 <= max_shift < nx/2 and
+ * max_shift <= 16 (nx = 128), 8 (nx = 64), 4 (nx = 32).
+ * Errors: INVALID_ARG, UNSUPPORTED_SIZE, OOM, CUDA; NUMERIC via the status word. */
+int bioem_score(bioem_ctx* ctx, const bioem_images* images, const bioem_projset* projset,
+                int max_shift, double* d_logP, double* d_logP_per_orient);
+
+/* Maximising grid parameters of every image (Sec. 3.8): the (orientation, PSF, displacement)
+ * with the largest ln L, and that ln L.  Ties go to the lowest (iq, ictf, dy, dx).
+ * All outputs [n_img] device arrays; any may be NULL except d_best_logL. */
+int bioem_best_params(bioem_ctx* ctx, const bioem_images* images, const bioem_projset* projset,
+                      int max_shift, int* d_best_q, int* d_best_ctf, int* d_best_dx, int* d_best_dy,
+                      double* d_best_logL);
+
+/* Both of the above from one pass over the grid (any output but d_logP may be NULL). */
+int bioem_score_all(bioem_ctx* ctx, const bioem_images* images, const bioem_projset* projset,
+                    int max_shift, double* d_logP, double* d_logP_per_orient, int* d_best_q,
+                    int* d_best_ctf, int* d_best_dx, int* d_best_dy, double* d_best_logL);
+
+/* Per-pair values for the parameter sets [ps_begin, ps_begin + ps_count):
+ *   d_pair_max [n_img][ps_count] = max_d ln L(w | p, d)
+ *   d_pair_lse [n_img][ps_count] = ln sum_d L(w | p, d)   (may be NULL)
+ * float64 device arrays. */
+int bioem_score_pairs(bioem_ctx* ctx, const bioem_images* images, const bioem_projset* projset,
+                      int max_shift, int ps_begin, int ps_count, double* d_pair_max,
+                      double* d_pair_lse);
+
+/* Synthetic maps (Sec. 3.8): the PSF-filtered projection I1 = F^-1[F(I0) CTF Env] (Eq. 5) of
+ * the model for n pairs (d_quats[i], ctfs[i]), written to d_out [n][ny][nx] float32 device.
+ * Same model arguments as bioem_project_model; ctfs is a HOST array of n entries. */
+int bioem_synthetic_maps(bioem_ctx* ctx, const float* d_atoms, int n_atoms, double sigma_A,
+                         const float* d_quats, const bioem_ctf* ctfs, int n, int nx, int ny,
+                         double pixel_A, float* d_out);
+
+/* Handle queries and release. */
+int bioem_images_count(const bioem_images* images);
+int bioem_projset_count(const bioem_projset* projset);
+void bioem_free_images(bioem_images* images);
+void bioem_free_projset(bioem_projset* projset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BIOEM_H */

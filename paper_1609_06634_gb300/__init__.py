@@ -1,0 +1,223 @@
+"""Python binding of the BioEM sm_103a scoring library (argument marshalling only).
+
+Every computation runs in the CUDA kernels behind the C ABI of ``include/bioem.h``; this module
+only checks tensor dtypes/devices, passes raw device pointers and the caller's CUDA stream, and
+wraps the library-owned handles.  PyTorch provides device memory and streams.  There is no CPU
+path: if the library is missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _native
+from ._native import CTF
+
+__all__ = ["BioEMError", "Context", "Images", "ProjSet", "prepare_images", "project_model", "score", "score_all",
+           "best_params", "score_pairs", "synthetic_maps", "ctf_array", "lib"]
+
+OK = 0
+ERR_INVALID_ARG, ERR_UNSUPPORTED_SIZE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NUMERIC = -1, -2, -3, -4, -5, -6
+
+
+def lib():
+    return _native.load()
+
+
+class BioEMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _check(ctx, code: int, what: str):
+    if code != OK:
+        detail = lib().bioem_last_error(ctx._h).decode() if ctx is not None and ctx._h else ""
+        raise BioEMError(code, f"{what}: {lib().bioem_status_string(code).decode()} {detail}".strip())
+
+
+def _dev_tensor(t, dtype, device, name, ndim=None, last=None):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or t.device != device:
+        raise BioEMError(ERR_INVALID_ARG, f"{name} must be a tensor on {device}")
+    if t.dtype != dtype:
+        raise BioEMError(ERR_INVALID_ARG, f"{name} must be {dtype}")
+    if ndim is not None and t.dim() != ndim:
+        raise BioEMError(ERR_INVALID_ARG, f"{name} must have {ndim} dimensions")
+    if last is not None and t.shape[-1] != last:
+        raise BioEMError(ERR_INVALID_ARG, f"{name} last dimension must be {last}")
+    return t.contiguous()
+
+
+def ctf_array(ctfs) -> ctypes.Array:
+    """Host array of bioem_ctf from rows (defocus_A, amp_contrast, bfactor_A2, voltage_kV)."""
+    rows = np.asarray(ctfs, dtype=np.float64).reshape(-1, 4)
+    arr = (CTF * len(rows))()
+    for i, r in enumerate(rows):
+        arr[i] = CTF(*[float(v) for v in r])
+    return arr
+
+
+class Context:
+    """A library context on one CUDA device, enqueueing on a CUDA stream (default: torch's current)."""
+
+    def __init__(self, device=0, stream=None):
+        torch = _torch()
+        self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        self._h = None
+        code = lib().bioem_create(ctypes.byref(h), self.device.index or 0, ctypes.c_void_p(self.stream.cuda_stream))
+        if code != OK:
+            raise BioEMError(code, "bioem_create failed")
+        self._h = h
+
+    def set_scratch_limit(self, nbytes: int):
+        _check(self, lib().bioem_set_scratch_limit(self._h, int(nbytes)), "set_scratch_limit")
+
+    def status(self) -> int:
+        """Synchronise the stream and read (and clear) the device status word."""
+        out = ctypes.c_int(0)
+        _check(self, lib().bioem_get_status(self._h, ctypes.byref(out)), "get_status")
+        return out.value
+
+    def close(self):
+        if self._h:
+            lib().bioem_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _Handle:
+    _free = None
+
+    def __init__(self, ctx: Context, h, **meta):
+        self.ctx = ctx
+        self._h = h
+        self.__dict__.update(meta)
+
+    def close(self):
+        if self._h:
+            getattr(lib(), self._free)(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Images(_Handle):
+    _free = "bioem_free_images"
+
+
+class ProjSet(_Handle):
+    _free = "bioem_free_projset"
+
+
+def prepare_images(ctx: Context, images, pixel_A: float) -> Images:
+    """bioem_prepare_images on a [n, ny, nx] float32 device tensor."""
+    torch = _torch()
+    t = _dev_tensor(images, torch.float32, ctx.device, "images", ndim=3)
+    h = ctypes.c_void_p()
+    n, ny, nx = t.shape
+    _check(ctx, lib().bioem_prepare_images(ctx._h, ctypes.c_void_p(t.data_ptr()), n, nx, ny, float(pixel_A),
+                                           ctypes.byref(h)), "prepare_images")
+    return Images(ctx, h, n_img=n, npix=nx, pixel_A=float(pixel_A))
+
+
+def project_model(ctx: Context, atoms, sigma_A: float, quats, ctfs, npix: int, pixel_A: float) -> ProjSet:
+    """bioem_project_model: atoms [n, 4] and quats [nq, 4] float32 device tensors, ctfs host rows."""
+    torch = _torch()
+    a = _dev_tensor(atoms, torch.float32, ctx.device, "atoms", ndim=2, last=4)
+    q = _dev_tensor(quats, torch.float32, ctx.device, "quats", ndim=2, last=4)
+    c = ctf_array(ctfs)
+    h = ctypes.c_void_p()
+    _check(ctx, lib().bioem_project_model(ctx._h, ctypes.c_void_p(a.data_ptr()), a.shape[0], float(sigma_A),
+                                          ctypes.c_void_p(q.data_ptr()), q.shape[0], c, len(c), npix, npix,
+                                          float(pixel_A), ctypes.byref(h)), "project_model")
+    return ProjSet(ctx, h, nq=q.shape[0], nctf=len(c), n_ps=q.shape[0] * len(c), npix=npix, pixel_A=float(pixel_A))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def score_all(ctx: Context, images: Images, projset: ProjSet, max_shift: int, per_orient: bool = False,
+              best: bool = False) -> dict:
+    """One pass over the grid: log P per image, optionally per orientation and maximising parameters."""
+    torch = _torch()
+    n = images.n_img
+    dev = ctx.device
+    out = {"logP": torch.empty(n, dtype=torch.float64, device=dev)}
+    if per_orient:
+        out["logP_orient"] = torch.empty((n, projset.nq), dtype=torch.float64, device=dev)
+    if best:
+        for k in ("best_q", "best_ctf", "best_dx", "best_dy"):
+            out[k] = torch.empty(n, dtype=torch.int32, device=dev)
+        out["best_logL"] = torch.empty(n, dtype=torch.float64, device=dev)
+    g = out.get
+    _check(ctx, lib().bioem_score_all(ctx._h, images._h, projset._h, int(max_shift), _ptr(g("logP")),
+                                      _ptr(g("logP_orient")), _ptr(g("best_q")), _ptr(g("best_ctf")),
+                                      _ptr(g("best_dx")), _ptr(g("best_dy")), _ptr(g("best_logL"))), "score_all")
+    return out
+
+
+def score(ctx: Context, images: Images, projset: ProjSet, max_shift: int, out=None):
+    """bioem_score: [n_img] float64 log P(image | model) on the device."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty(images.n_img, dtype=torch.float64, device=ctx.device)
+    _check(ctx, lib().bioem_score(ctx._h, images._h, projset._h, int(max_shift), _ptr(out), ctypes.c_void_p(0)),
+           "score")
+    return out
+
+
+def best_params(ctx: Context, images: Images, projset: ProjSet, max_shift: int) -> dict:
+    torch = _torch()
+    n = images.n_img
+    out = {k: torch.empty(n, dtype=torch.int32, device=ctx.device) for k in ("q", "ctf", "dx", "dy")}
+    out["logL"] = torch.empty(n, dtype=torch.float64, device=ctx.device)
+    _check(ctx, lib().bioem_best_params(ctx._h, images._h, projset._h, int(max_shift), _ptr(out["q"]), _ptr(out["ctf"]),
+                                        _ptr(out["dx"]), _ptr(out["dy"]), _ptr(out["logL"])), "best_params")
+    return out
+
+
+def score_pairs(ctx: Context, images: Images, projset: ProjSet, max_shift: int, ps_begin: int = 0,
+                ps_count: int | None = None):
+    """Per-pair max_d ln L and ln sum_d L, [n_img, ps_count] float64."""
+    torch = _torch()
+    if ps_count is None:
+        ps_count = projset.n_ps - ps_begin
+    pmax = torch.empty((images.n_img, ps_count), dtype=torch.float64, device=ctx.device)
+    plse = torch.empty_like(pmax)
+    _check(ctx, lib().bioem_score_pairs(ctx._h, images._h, projset._h, int(max_shift), int(ps_begin), int(ps_count),
+                                        _ptr(pmax), _ptr(plse)), "score_pairs")
+    return pmax, plse
+
+
+def synthetic_maps(ctx: Context, atoms, sigma_A: float, quats, ctfs, npix: int, pixel_A: float):
+    """bioem_synthetic_maps: I1 for pairs (quats[i], ctfs[i]) as a [n, npix, npix] float32 device tensor."""
+    torch = _torch()
+    a = _dev_tensor(atoms, torch.float32, ctx.device, "atoms", ndim=2, last=4)
+    q = _dev_tensor(quats, torch.float32, ctx.device, "quats", ndim=2, last=4)
+    c = ctf_array(ctfs)
+    if len(c) != q.shape[0]:
+        raise BioEMError(ERR_INVALID_ARG, "one CTF row per quaternion")
+    out = torch.empty((q.shape[0], npix, npix), dtype=torch.float32, device=ctx.device)
+    _check(ctx, lib().bioem_synthetic_maps(ctx._h, ctypes.c_void_p(a.data_ptr()), a.shape[0], float(sigma_A),
+                                           ctypes.c_void_p(q.data_ptr()), c, q.shape[0], npix, npix, float(pixel_A),
+                                           _ptr(out)), "synthetic_maps")
+    return out

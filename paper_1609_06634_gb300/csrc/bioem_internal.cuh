@@ -1,0 +1,103 @@
+// Internal declarations shared by the translation units of the BioEM sm_103a library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/bioem.h"
+
+// ------------------------------------------------------------------ handles
+struct bioem_ctx {
+    int device;
+    cudaStream_t stream;
+    int num_sms;
+    int* d_status;                      // device status word (BIOEM_ERR_* bits folded to a code)
+    unsigned long long scratch_limit;   // bytes allowed for per-pair records
+    // per-pair record scratch (grown on demand)
+    void* d_rec;
+    size_t rec_bytes;
+    // per-image accumulators of the wave reduction
+    void* d_acc;
+    size_t acc_bytes;
+    // twiddle tables (float2, W_N^k = exp(-2 pi i k / N)) for the direct transforms, by N
+    float2* d_tw[5];
+    char last_error[256];
+};
+
+struct bioem_images {
+    bioem_ctx* ctx;
+    int n_img, nx, ny;
+    double pixel_A;
+    float2* d_spec;   // [n_img][ny][nx/2] unit-norm half spectrum (kx < nx/2), DC = 0
+    float2* d_nyq;    // [n_img][ny] Nyquist column kx = nx/2
+    double* d_kA;     // [n_img] (3-n)/2 ln A + c(n)
+};
+
+struct bioem_projset {
+    bioem_ctx* ctx;
+    int nq, nctf, n_ps, nx, ny;
+    double pixel_A;
+    float2* d_spec;   // [n_ps][ny][nx/2] unit-norm PSF-filtered projection spectrum, DC = 0
+    float2* d_nyq;    // [n_ps][ny]
+    double* d_kB;     // [n_ps] -1/2 ln B
+};
+
+// ------------------------------------------------------------------ status codes inside kernels
+#define BIOEM_DEV_NUMERIC 1
+
+// ------------------------------------------------------------------ helpers
+__host__ __device__ inline int bioem_size_index(int n) {
+    switch (n) {
+        case 32: return 0;
+        case 64: return 1;
+        case 96: return 2;
+        case 128: return 3;
+        case 192: return 4;
+        default: return -1;
+    }
+}
+
+__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// conj(a) * b
+__device__ __forceinline__ float2 c_mulc(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
+}
+__device__ __forceinline__ float2 c_scale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+// ------------------------------------------------------------------ launchers (defined in .cu files)
+// prep_project.cu
+int bioem_launch_prepare(bioem_ctx* ctx, const float* d_images, bioem_images* im);
+int bioem_launch_project(bioem_ctx* ctx, const float* d_atoms, int n_atoms, double sigma_A,
+                         const float* d_quats, int nq, const bioem_ctf* ctfs, int nctf,
+                         bioem_projset* ps);
+int bioem_launch_synthetic(bioem_ctx* ctx, const float* d_atoms, int n_atoms, double sigma_A,
+                           const float* d_quats, const bioem_ctf* ctfs, int n, int npix,
+                           double pixel_A, float* d_out);
+double bioem_log_norm_constant(int n);
+
+// score.cu
+struct bioem_score_out {
+    double* logP;
+    double* logP_orient;
+    int* best_q;
+    int* best_ctf;
+    int* best_dx;
+    int* best_dy;
+    double* best_logL;
+    double* pair_max;   // score_pairs mode
+    double* pair_lse;
+    int ps_begin, ps_count;
+};
+int bioem_score_supported(int npix, int max_shift);
+int bioem_launch_score(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, int max_shift,
+                       const bioem_score_out& out);
+int bioem_upload_score_twiddles(bioem_ctx* ctx);
+
+// abi.cu
+int bioem_set_error(bioem_ctx* ctx, int code, const char* fmt, ...);
+int bioem_check_cuda(bioem_ctx* ctx, cudaError_t e, const char* what);
+float2* bioem_twiddles(bioem_ctx* ctx, int npix);

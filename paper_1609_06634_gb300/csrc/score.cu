@@ -1,0 +1,629 @@
+// Fused scoring kernel: per (image, parameter set) pair, the Fourier-space product, the inverse
+// transform evaluated on the displacement window only, and the closed-form likelihood with a
+// log-sum-exp over displacements (Sec. 3.3, Eqs. 11-12; Sec. 3.9 and Sec. 5 note that the product,
+// the inverse FFT and the likelihood were three kernels with the correlation map stored between
+// them, and that only some output coefficients are needed: here they are one kernel and the map
+// never leaves the SM).
+//
+// Spectra (both unit-norm, DC = 0, half spectrum kx = 0..N/2):
+//   rho(d) = X(d) / sqrt(A B) = Re sum_{ky} sum_{kx<=N/2} w_kx conj(O(k)) C(k) exp(+2 pi i k.d / N)
+// with w = 1 on the kx = 0 and kx = N/2 columns, 2 elsewhere.  Evaluated in two stages:
+//   stage A (per column kx, along ky):  Q(dy, kx) = sum_ky conj(O) C exp(+2 pi i ky dy / N)
+//   stage B (per row dy, along kx):     rho(dy, dx) = Re sum_kx w_kx Q(dy, kx) exp(+2 pi i kx dx / N)
+// each as a pruned transform: the N (or N/2) inputs split into R interleaved sub-sequences of
+// length L = 16, each transformed by an in-register radix-2 FFT, then recombined with twiddles for
+// the 2 SMAX + 1 wanted outputs only.
+//
+// Likelihood (closed form of Eq. 8 integrated over N, mu, lambda):
+//   ln L(d) = kA + kB + (3 - n)/2 ln(1 - rho(d)^2),  kA = (3-n)/2 ln A + c(n),  kB = -1/2 ln B.
+// Per pair the kernel records t_min = min_d ln(1 - rho^2), s = sum_d exp((3-n)/2 (t(d) - t_min))
+// and the argmin d; a float64 reduction (k_reduce_wave) turns the records into per-image and
+// per-orientation log-sum-exps and maximising parameters.
+#include <math.h>
+#include <stdio.h>
+
+#include "bioem_internal.cuh"
+
+namespace {
+
+constexpr int L = 16;   // sub-transform length
+
+// W_M^t = exp(+2 pi i t / M), uploaded once per device.
+__constant__ float2 c_w16[16];
+__constant__ float2 c_w32[32];
+__constant__ float2 c_w64[64];
+__constant__ float2 c_w128[128];
+
+template <int M>
+__device__ __forceinline__ float2 cw(int t) {
+    if constexpr (M == 16) return c_w16[t];
+    else if constexpr (M == 32) return c_w32[t];
+    else if constexpr (M == 64) return c_w64[t];
+    else return c_w128[t];
+}
+
+template <int M>
+__device__ __forceinline__ const float2* cw_table() {
+    if constexpr (M == 16) return c_w16;
+    else if constexpr (M == 32) return c_w32;
+    else if constexpr (M == 64) return c_w64;
+    else return c_w128;
+}
+
+// d * W_LL^t for a compile-time exponent t < LL / 2.
+template <int LL, int T>
+__device__ __forceinline__ float2 twiddle_mul(float2 d) {
+    if constexpr (T == 0) {
+        return d;
+    } else if constexpr (4 * T == LL) {          // W^(LL/4) = i
+        return make_float2(-d.y, d.x);
+    } else if constexpr (8 * T == LL) {          // (1 + i) / sqrt 2
+        const float r = 0.70710678118654752f;
+        return make_float2((d.x - d.y) * r, (d.x + d.y) * r);
+    } else if constexpr (8 * T == 3 * LL) {      // (-1 + i) / sqrt 2
+        const float r = 0.70710678118654752f;
+        return make_float2(-(d.x + d.y) * r, (d.x - d.y) * r);
+    } else {
+        return c_mul(d, cw<LL>(T));
+    }
+}
+
+template <int LL, int HALF, int BLK, int J>
+__device__ __forceinline__ void dif_butterflies(float2 (&x)[LL]) {
+    if constexpr (BLK < LL) {
+        if constexpr (J < HALF) {
+            const float2 a = x[BLK + J], b = x[BLK + J + HALF];
+            x[BLK + J] = c_add(a, b);
+            x[BLK + J + HALF] = twiddle_mul<LL, J * (LL / (2 * HALF))>(c_sub(a, b));
+            dif_butterflies<LL, HALF, BLK, J + 1>(x);
+        } else {
+            dif_butterflies<LL, HALF, BLK + 2 * HALF, 0>(x);
+        }
+    }
+}
+
+template <int LL, int HALF>
+__device__ __forceinline__ void dif_stages(float2 (&x)[LL]) {
+    if constexpr (HALF >= 1) {
+        dif_butterflies<LL, HALF, 0, 0>(x);
+        dif_stages<LL, HALF / 2>(x);
+    }
+}
+
+// In-register DFT y[u] = sum_a x[a] W_LL^(a u), radix-2 decimation in frequency; on return
+// y[u] is stored at x[bitrev(u)].
+template <int LL>
+__device__ __forceinline__ void fft_dif(float2 (&x)[LL]) {
+    dif_stages<LL, LL / 2>(x);
+}
+
+__host__ __device__ constexpr int bitrev(int u, int bits) {
+    int r = 0;
+    for (int i = 0; i < bits; ++i) r |= ((u >> i) & 1) << (bits - 1 - i);
+    return r;
+}
+__host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
+__host__ __device__ constexpr int pmod(int a, int m) { return ((a % m) + m) % m; }
+
+template <int N_, int SMAX_, int PB_>
+struct Cfg {
+    static constexpr int N = N_;
+    static constexpr int SMAX = SMAX_;
+    static constexpr int PB = PB_;             // pairs per batch
+    static constexpr int NC = N / 2;
+    static constexpr int NCOL = NC + 1;        // stage-A columns per pair (kx = 0..N/2)
+    static constexpr int NS = 2 * SMAX + 1;    // displacements per axis
+    static constexpr int NROW = 2 * SMAX;      // stage-B transform rows per pair (dy < SMAX)
+    static constexpr int THREADS = PB * NROW;
+    static constexpr int R = N / L;            // sub-sequences per transform
+    static constexpr int QS = NCOL;            // Q row stride (complex); odd -> conflict-free columns
+    static constexpr int TASKS_A = PB * NCOL;
+    static constexpr int NDIR = PB * NS;       // outputs of the dy = +SMAX row, evaluated directly
+    static constexpr size_t SM_IMG = (size_t)N * NC * sizeof(float2);
+    static constexpr size_t SM_NYQ = (size_t)N * sizeof(float2);
+    static constexpr size_t SM_Q = (size_t)PB * NS * QS * sizeof(float2);
+    static constexpr size_t SM_TW = (size_t)N * sizeof(float2);
+    static constexpr size_t SM_ROW = (size_t)PB * NROW * (2 * sizeof(float) + sizeof(int));
+    static constexpr size_t SM_DIR = (size_t)NDIR * sizeof(float);
+    static constexpr size_t SMEM = SM_IMG + SM_NYQ + SM_Q + SM_TW + SM_ROW + SM_DIR;
+};
+
+// acc[mi] += W_N^(b m) y[m mod L] for m = mi - SMAX (complex accumulate)
+template <int N, int SMAX, int B, int MI>
+__device__ __forceinline__ void combine_complex(float2 (&acc)[2 * SMAX + 1], const float2 (&x)[L]) {
+    if constexpr (MI < 2 * SMAX + 1) {
+        constexpr int m = MI - SMAX;
+        constexpr int u = bitrev(pmod(m, L), ilog2(L));
+        constexpr int t = pmod(B * m, N);
+        if constexpr (t == 0) {
+            acc[MI] = c_add(acc[MI], x[u]);
+        } else {
+            const float2 w = cw<N>(t);
+            acc[MI].x = fmaf(w.x, x[u].x, fmaf(-w.y, x[u].y, acc[MI].x));
+            acc[MI].y = fmaf(w.x, x[u].y, fmaf(w.y, x[u].x, acc[MI].y));
+        }
+        combine_complex<N, SMAX, B, MI + 1>(acc, x);
+    }
+}
+
+// acc[mi] += Re(W_N^(b m) y[m mod L])
+template <int N, int SMAX, int B, int MI>
+__device__ __forceinline__ void combine_real(float (&acc)[2 * SMAX + 1], const float2 (&x)[L]) {
+    if constexpr (MI < 2 * SMAX + 1) {
+        constexpr int m = MI - SMAX;
+        constexpr int u = bitrev(pmod(m, L), ilog2(L));
+        constexpr int t = pmod(B * m, N);
+        if constexpr (t == 0) {
+            acc[MI] += x[u].x;
+        } else {
+            const float2 w = cw<N>(t);
+            acc[MI] = fmaf(w.x, x[u].x, fmaf(-w.y, x[u].y, acc[MI]));
+        }
+        combine_real<N, SMAX, B, MI + 1>(acc, x);
+    }
+}
+
+// Stage A for one column: sub-sequences b = 0..R-1 (rows ky = b + R a).
+template <class C, int B>
+__device__ __forceinline__ void stage_a_sub(float2 (&acc)[C::NS], const float2* __restrict__ img_col,
+                                            const float2* __restrict__ ps_col, int stride) {
+    if constexpr (B < C::R) {
+        float2 x[L];
+#pragma unroll
+        for (int a = 0; a < L; ++a) {
+            const int ky = B + C::R * a;
+            const float2 o = img_col[ky * stride];
+            const float2 c = __ldg(ps_col + ky * stride);
+            x[a] = c_mulc(o, c);
+        }
+        fft_dif<L>(x);
+        combine_complex<C::N, C::SMAX, B, 0>(acc, x);
+        stage_a_sub<C, B + 1>(acc, img_col, ps_col, stride);
+    }
+}
+
+// Stage B for one row: inputs R(kx) = w_kx Q(dy, kx) for kx < N/2 (kx = b + R a).
+template <class C, int B>
+__device__ __forceinline__ void stage_b_sub(float (&acc)[C::NS], const float2* __restrict__ qrow) {
+    if constexpr (B < C::R) {
+        float2 x[L];
+#pragma unroll
+        for (int a = 0; a < L; ++a) {
+            const int kx = B + C::R * a;
+            if (kx == 0) x[a] = make_float2(qrow[0].x, 0.f);
+            else if (kx < C::NC) x[a] = c_scale(qrow[kx], 2.f);
+            else x[a] = make_float2(0.f, 0.f);
+        }
+        fft_dif<L>(x);
+        combine_real<C::N, C::SMAX, B, 0>(acc, x);
+        stage_b_sub<C, B + 1>(acc, qrow);
+    }
+}
+
+struct Part {
+    float t;   // min ln(1 - rho^2)
+    float s;   // sum exp(c1 (t(d) - t))
+    int d;     // index of the minimum, (dy + SMAX) * NS + (dx + SMAX)
+};
+
+__device__ __forceinline__ Part merge(Part a, Part b, float c1) {
+    if (b.t > a.t || (b.t == a.t && b.d > a.d)) {
+        const Part tmp = a;
+        a = b;
+        b = tmp;
+    }
+    // now b.t <= a.t (b holds the minimum, lowest index on ties)
+    if (!(a.t < INFINITY)) return b;
+    Part r;
+    r.t = b.t;
+    r.d = b.d;
+    r.s = b.s + a.s * __expf(c1 * (a.t - b.t));
+    return r;
+}
+
+__device__ __forceinline__ float loglik_t(float rho, int* status) {
+    float r2 = rho * rho;
+    if (r2 >= 1.0f) {
+        atomicOr(status, BIOEM_DEV_NUMERIC);
+        r2 = 1.0f - 5.9604645e-8f;
+    }
+    return log1pf(-r2);
+}
+
+template <class C>
+__global__ void __launch_bounds__(C::THREADS, 1)
+k_score(const float2* __restrict__ img_spec, const float2* __restrict__ img_nyq, int n_img,
+        const float2* __restrict__ ps_spec, const float2* __restrict__ ps_nyq, int ps_begin, int ps_count,
+        int chunk, int n_items, int s, float c1, float* __restrict__ rec_t, float* __restrict__ rec_s,
+        int* __restrict__ rec_d, int* __restrict__ status) {
+    constexpr int N = C::N, NC = C::NC, NS = C::NS, SMAX = C::SMAX, NROW = C::NROW;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2* img_s = reinterpret_cast<float2*>(smem);
+    float2* nyq_s = reinterpret_cast<float2*>(smem + C::SM_IMG);
+    float2* q_s = reinterpret_cast<float2*>(smem + C::SM_IMG + C::SM_NYQ);
+    float2* tw_s = reinterpret_cast<float2*>(smem + C::SM_IMG + C::SM_NYQ + C::SM_Q);
+    float* row_t = reinterpret_cast<float*>(smem + C::SM_IMG + C::SM_NYQ + C::SM_Q + C::SM_TW);
+    float* row_s = row_t + C::PB * NROW;
+    int* row_d = reinterpret_cast<int*>(row_s + C::PB * NROW);
+    float* dir_t = reinterpret_cast<float*>(row_d + C::PB * NROW);
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    constexpr int NWARPS = (C::THREADS + 31) / 32;
+    for (int i = tid; i < N; i += C::THREADS) tw_s[i] = cw_table<N>()[i];
+
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int ci = item / n_img;
+        const int w = item - ci * n_img;
+        const int lo = ci * chunk;
+        const int hi = min(lo + chunk, ps_count);
+        __syncthreads();   // previous item's readers of img_s are done
+        {
+            const float4* src = reinterpret_cast<const float4*>(img_spec + (size_t)w * N * NC);
+            float4* dst = reinterpret_cast<float4*>(img_s);
+            for (int i = tid; i < N * NC / 2; i += C::THREADS) dst[i] = __ldg(src + i);
+            for (int i = tid; i < N; i += C::THREADS) nyq_s[i] = img_nyq[(size_t)w * N + i];
+        }
+        __syncthreads();
+        for (int p0 = lo; p0 < hi; p0 += C::PB) {
+            // ---------------- stage A: one column of one pair per task
+            for (int task = tid; task < C::TASKS_A; task += C::THREADS) {
+                const int j = task / C::NCOL;
+                const int kx = task - j * C::NCOL;
+                const int p = min(p0 + j, hi - 1);
+                const size_t gp = (size_t)(ps_begin + p);
+                const bool nyq = (kx == NC);
+                const float2* img_col = nyq ? nyq_s : img_s + kx;
+                const float2* ps_col = nyq ? ps_nyq + gp * N : ps_spec + gp * N * NC + kx;
+                const int stride = nyq ? 1 : NC;
+                float2 acc[NS];
+#pragma unroll
+                for (int m = 0; m < NS; ++m) acc[m] = make_float2(0.f, 0.f);
+                stage_a_sub<C, 0>(acc, img_col, ps_col, stride);
+                float2* qdst = q_s + (size_t)j * NS * C::QS + kx;
+#pragma unroll
+                for (int m = 0; m < NS; ++m) qdst[m * C::QS] = acc[m];
+            }
+            __syncthreads();
+            // ---------------- stage B: one row (dy = -SMAX .. SMAX-1) of one pair per thread
+            {
+                const int j = tid / NROW;
+                const int r = tid - j * NROW;
+                const float2* qrow = q_s + ((size_t)j * NS + r) * C::QS;
+                float acc[NS];
+#pragma unroll
+                for (int m = 0; m < NS; ++m) acc[m] = 0.f;
+                stage_b_sub<C, 0>(acc, qrow);
+                const float qn = qrow[NC].x;   // Nyquist column, weight 1, phase (-1)^dx
+                const bool row_ok = abs(r - SMAX) <= s;
+                float tmin = INFINITY;
+                int arg = 0x7fffffff;
+#pragma unroll
+                for (int m = 0; m < NS; ++m) {
+                    const float rho = acc[m] + (((m - SMAX) & 1) ? -qn : qn);
+                    const bool ok = row_ok && abs(m - SMAX) <= s;
+                    const float t = ok ? loglik_t(rho, status) : INFINITY;
+                    acc[m] = t;
+                    if (t < tmin) {
+                        tmin = t;
+                        arg = r * NS + m;
+                    }
+                }
+                float ssum = 0.f;
+#pragma unroll
+                for (int m = 0; m < NS; ++m) ssum += (acc[m] < INFINITY) ? __expf(c1 * (acc[m] - tmin)) : 0.f;
+                row_t[tid] = tmin;
+                row_s[tid] = ssum;
+                row_d[tid] = arg;
+            }
+            // ---------------- the dy = +SMAX row, one output per task, evaluated directly
+            for (int i = tid; i < C::NDIR; i += C::THREADS) {
+                const int j = i / NS;
+                const int mi = i - j * NS;
+                const int dx = mi - SMAX;
+                const float2* qrow = q_s + ((size_t)j * NS + 2 * SMAX) * C::QS;
+                float accv = 0.f;
+                int idx = pmod(dx, N);
+                const int step = idx;
+                for (int kx = 1; kx < NC; ++kx) {
+                    const float2 v = qrow[kx];
+                    const float2 wv = tw_s[idx];
+                    accv = fmaf(v.x, wv.x, fmaf(-v.y, wv.y, accv));
+                    idx += step;
+                    idx -= (idx >= N) ? N : 0;
+                }
+                const float rho = qrow[0].x + 2.f * accv + ((dx & 1) ? -qrow[NC].x : qrow[NC].x);
+                const bool ok = SMAX <= s && abs(dx) <= s;
+                dir_t[i] = ok ? loglik_t(rho, status) : INFINITY;
+            }
+            __syncthreads();
+            // ---------------- combine the pieces of each pair (one warp per pair)
+            for (int j = warp; j < C::PB; j += NWARPS) {
+                const int p = p0 + j;
+                if (p >= hi) continue;
+                Part acc{INFINITY, 0.f, 0x7fffffff};
+                for (int r = lane; r < NROW; r += 32) acc = merge(acc, Part{row_t[j * NROW + r], row_s[j * NROW + r], row_d[j * NROW + r]}, c1);
+                for (int mi = lane; mi < NS; mi += 32) {
+                    const float t = dir_t[j * NS + mi];
+                    acc = merge(acc, Part{t, t < INFINITY ? 1.f : 0.f, 2 * SMAX * NS + mi}, c1);
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    Part o;
+                    o.t = __shfl_xor_sync(0xffffffffu, acc.t, off);
+                    o.s = __shfl_xor_sync(0xffffffffu, acc.s, off);
+                    o.d = __shfl_xor_sync(0xffffffffu, acc.d, off);
+                    acc = merge(acc, o, c1);   // merge orders its operands, so both lanes agree
+                }
+                if (lane == 0) {
+                    const size_t o = (size_t)w * ps_count + p;
+                    rec_t[o] = acc.t;
+                    rec_s[o] = acc.s;
+                    rec_d[o] = acc.d;
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------- reductions (float64)
+struct Acc {
+    double M;    // running max
+    double S;    // sum exp(. - M)
+    double bv;   // best ln L
+    int bp;      // its parameter set
+    int bd;      // its displacement index
+};
+
+__device__ __forceinline__ void acc_add(Acc& a, double m, double s, int p, int d) {
+    if (!(m > -INFINITY)) return;
+    if (m > a.M) {
+        a.S = a.S * exp(a.M - m) + s;
+        a.M = m;
+    } else {
+        a.S += s * exp(m - a.M);
+    }
+    if (m > a.bv || (m == a.bv && p < a.bp)) {
+        a.bv = m;
+        a.bp = p;
+        a.bd = d;
+    }
+}
+
+__device__ __forceinline__ void acc_merge(Acc& a, const Acc& b) {
+    if (b.M > -INFINITY) {
+        if (b.M > a.M) {
+            a.S = a.S * exp(a.M - b.M) + b.S;
+            a.M = b.M;
+        } else {
+            a.S += b.S * exp(b.M - a.M);
+        }
+    }
+    if (b.bv > a.bv || (b.bv == a.bv && b.bp < a.bp)) {
+        a.bv = b.bv;
+        a.bp = b.bp;
+        a.bd = b.bd;
+    }
+}
+
+constexpr int kRedThreads = 256;
+
+// One block per image: fold the wave's pair records into the image's running accumulator and,
+// if requested, write the per-orientation posteriors of the wave's orientations.
+__global__ void __launch_bounds__(kRedThreads) k_reduce_wave(
+    const float* __restrict__ rec_t, const float* __restrict__ rec_s, const int* __restrict__ rec_d,
+    const double* __restrict__ kA, const double* __restrict__ kB, int ps_begin, int wave_len, int nctf,
+    int nq, double c1, double log_norm_orient, Acc* __restrict__ acc, int first, double* __restrict__ logP_orient) {
+    __shared__ Acc red[kRedThreads];
+    const int w = blockIdx.x;
+    const double ka = kA[w];
+    Acc a{-INFINITY, 0.0, -INFINITY, 0x7fffffff, 0};
+    const size_t base = (size_t)w * wave_len;
+    for (int p = threadIdx.x; p < wave_len; p += blockDim.x) {
+        const double m = ka + kB[ps_begin + p] + c1 * (double)rec_t[base + p];
+        acc_add(a, m, (double)rec_s[base + p], ps_begin + p, rec_d[base + p]);
+    }
+    red[threadIdx.x] = a;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) acc_merge(red[threadIdx.x], red[threadIdx.x + st]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        Acc r = red[0];
+        if (!first) {
+            Acc prev = acc[w];
+            acc_merge(prev, r);
+            r = prev;
+        }
+        acc[w] = r;
+    }
+    if (logP_orient) {
+        const int q0 = ps_begin / nctf;
+        for (int ql = threadIdx.x; ql < wave_len / nctf; ql += blockDim.x) {
+            double M = -INFINITY, S = 0.0;
+            for (int c = 0; c < nctf; ++c) {
+                const int p = ql * nctf + c;
+                const double m = ka + kB[ps_begin + p] + c1 * (double)rec_t[base + p];
+                const double s = rec_s[base + p];
+                if (!(m > -INFINITY)) continue;
+                if (m > M) { S = S * exp(M - m) + s; M = m; }
+                else S += s * exp(m - M);
+            }
+            logP_orient[(size_t)w * nq + q0 + ql] = M + log(S) - log_norm_orient;
+        }
+    }
+}
+
+__global__ void k_finalize(const Acc* __restrict__ acc, int n_img, double log_norm, int nctf, int nsk, int smax,
+                           double* logP, int* best_q, int* best_ctf, int* best_dx, int* best_dy, double* best_logL) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= n_img) return;
+    const Acc a = acc[w];
+    if (logP) logP[w] = a.M + log(a.S) - log_norm;
+    if (best_q) best_q[w] = a.bp / nctf;
+    if (best_ctf) best_ctf[w] = a.bp % nctf;
+    if (best_dy) best_dy[w] = a.bd / nsk - smax;
+    if (best_dx) best_dx[w] = a.bd % nsk - smax;
+    if (best_logL) best_logL[w] = a.bv;
+}
+
+// pair_max[w][col0 + p] = max_d ln L and pair_lse[w][col0 + p] = ln sum_d L for the wave's records.
+__global__ void k_pairs_out(const float* __restrict__ rec_t, const float* __restrict__ rec_s,
+                            const double* __restrict__ kA, const double* __restrict__ kB, int n_img, int ps_begin,
+                            int count, double c1, double* pair_max, double* pair_lse, int row_stride, int col0) {
+    const size_t total = (size_t)n_img * count;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int w = (int)(i / count);
+        const int p = (int)(i - (size_t)w * count);
+        const double m = kA[w] + kB[ps_begin + p] + c1 * (double)rec_t[i];
+        const size_t o = (size_t)w * row_stride + col0 + p;
+        pair_max[o] = m;
+        if (pair_lse) pair_lse[o] = m + log((double)rec_s[i]);
+    }
+}
+
+// ---------------------------------------------------------------------------- host side
+template <class C>
+int run_score(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, int max_shift,
+              const bioem_score_out& out) {
+    const int n_img = im->n_img;
+    const int n = C::N * C::N;
+    const int nsk = C::NS;
+    const bool pairs_mode = out.pair_max != nullptr;
+    const int range_begin = pairs_mode ? out.ps_begin : 0;
+    const int range_len = pairs_mode ? out.ps_count : ps->n_ps;
+    const int nctf = ps->nctf;
+    if (n_img == 0 || range_len == 0) return BIOEM_OK;
+
+    // wave length: records of n_img x wave must fit the scratch limit; aligned to whole orientations
+    const unsigned long long per_ps = (unsigned long long)n_img * 12ull;
+    long long wave = (long long)(ctx->scratch_limit / per_ps);
+    if (!pairs_mode) wave -= wave % nctf;
+    if (wave < (pairs_mode ? 1 : nctf)) wave = pairs_mode ? 1 : nctf;
+    if (wave > range_len) wave = range_len;
+    const size_t rec_need = (size_t)n_img * (size_t)wave * 12;
+    if (ctx->rec_bytes < rec_need) {
+        if (ctx->d_rec) cudaFreeAsync(ctx->d_rec, ctx->stream);
+        ctx->d_rec = nullptr;
+        ctx->rec_bytes = 0;
+        if (cudaMallocAsync(&ctx->d_rec, rec_need, ctx->stream) != cudaSuccess)
+            return bioem_set_error(ctx, BIOEM_ERR_OOM, "record scratch of %zu bytes", rec_need);
+        ctx->rec_bytes = rec_need;
+    }
+    const size_t acc_need = sizeof(Acc) * (size_t)n_img;
+    if (!pairs_mode && ctx->acc_bytes < acc_need) {
+        if (ctx->d_acc) cudaFreeAsync(ctx->d_acc, ctx->stream);
+        ctx->d_acc = nullptr;
+        ctx->acc_bytes = 0;
+        if (cudaMallocAsync(&ctx->d_acc, acc_need, ctx->stream) != cudaSuccess)
+            return bioem_set_error(ctx, BIOEM_ERR_OOM, "accumulator scratch");
+        ctx->acc_bytes = acc_need;
+    }
+    float* rec_t = reinterpret_cast<float*>(ctx->d_rec);
+    float* rec_s = rec_t + (size_t)n_img * wave;
+    int* rec_d = reinterpret_cast<int*>(rec_s + (size_t)n_img * wave);
+
+    const size_t smem = C::SMEM;
+    if (cudaFuncSetAttribute(k_score<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return bioem_set_error(ctx, BIOEM_ERR_CUDA, "shared memory attribute (%zu bytes)", smem);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score<C>, C::THREADS, smem) != cudaSuccess || per_sm < 1)
+        return bioem_set_error(ctx, BIOEM_ERR_CUDA, "occupancy query");
+    const int slots = per_sm * ctx->num_sms;
+    const float c1f = 0.5f * (3.0f - (float)n);
+    const double c1 = 0.5 * (3.0 - (double)n);
+    const int S = (2 * max_shift + 1) * (2 * max_shift + 1);
+
+    for (long long w0 = 0; w0 < range_len; w0 += wave) {
+        const int wl = (int)(range_len - w0 < wave ? range_len - w0 : wave);
+        const int wbegin = range_begin + (int)w0;
+        // chunk: enough work items to keep every slot busy, at most 512 parameter sets
+        const long long target_items = 4ll * slots;
+        long long per_img = (target_items + n_img - 1) / n_img;
+        long long chunk = (wl + per_img - 1) / per_img;
+        chunk = ((chunk + C::PB - 1) / C::PB) * C::PB;
+        if (chunk > 512) chunk = 512;
+        if (chunk < C::PB) chunk = C::PB;
+        const long long n_chunks = (wl + chunk - 1) / chunk;
+        const long long n_items = n_chunks * n_img;
+        if (n_items > 0x7fffffffll) return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE, "too many work items");
+        const int grid = (int)(n_items < slots ? n_items : slots);
+        k_score<C><<<grid, C::THREADS, smem, ctx->stream>>>(im->d_spec, im->d_nyq, n_img, ps->d_spec, ps->d_nyq, wbegin,
+                                                             wl, (int)chunk, (int)n_items, max_shift, c1f, rec_t, rec_s,
+                                                             rec_d, ctx->d_status);
+        int rc = bioem_check_cuda(ctx, cudaGetLastError(), "k_score");
+        if (rc) return rc;
+        if (pairs_mode) {
+            k_pairs_out<<<1024, 256, 0, ctx->stream>>>(rec_t, rec_s, im->d_kA, ps->d_kB, n_img, wbegin, wl, c1,
+                                                       out.pair_max, out.pair_lse, range_len, (int)w0);
+        } else {
+            const double log_norm_orient = log((double)nctf * S);
+            k_reduce_wave<<<n_img, kRedThreads, 0, ctx->stream>>>(rec_t, rec_s, rec_d, im->d_kA, ps->d_kB, wbegin, wl,
+                                                                  nctf, ps->nq, c1, log_norm_orient,
+                                                                  reinterpret_cast<Acc*>(ctx->d_acc), w0 == 0,
+                                                                  out.logP_orient);
+        }
+        rc = bioem_check_cuda(ctx, cudaGetLastError(), "reduction");
+        if (rc) return rc;
+    }
+    if (!pairs_mode) {
+        const double log_norm = log((double)ps->n_ps * S);
+        k_finalize<<<(n_img + 255) / 256, 256, 0, ctx->stream>>>(reinterpret_cast<const Acc*>(ctx->d_acc), n_img, log_norm,
+                                                                  nctf, nsk, C::SMAX, out.logP, out.best_q, out.best_ctf,
+                                                                  out.best_dx, out.best_dy, out.best_logL);
+        return bioem_check_cuda(ctx, cudaGetLastError(), "k_finalize");
+    }
+    return BIOEM_OK;
+}
+
+using C32_4 = Cfg<32, 4, 32>;
+using C64_4 = Cfg<64, 4, 32>;
+using C64_8 = Cfg<64, 8, 16>;
+using C128_4 = Cfg<128, 4, 32>;
+using C128_16 = Cfg<128, 16, 8>;
+
+}  // namespace
+
+int bioem_score_supported(int npix, int max_shift) {
+    if (max_shift < 0 || 2 * max_shift >= npix) return 0;
+    switch (npix) {
+        case 32: return max_shift <= 4;
+        case 64: return max_shift <= 8;
+        case 128: return max_shift <= 16;
+        default: return 0;
+    }
+}
+
+int bioem_launch_score(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, int max_shift,
+                       const bioem_score_out& out) {
+    switch (im->nx) {
+        case 32: return run_score<C32_4>(ctx, im, ps, max_shift, out);
+        case 64: return max_shift <= 4 ? run_score<C64_4>(ctx, im, ps, max_shift, out)
+                                       : run_score<C64_8>(ctx, im, ps, max_shift, out);
+        case 128: return max_shift <= 4 ? run_score<C128_4>(ctx, im, ps, max_shift, out)
+                                        : run_score<C128_16>(ctx, im, ps, max_shift, out);
+        default: return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE, "unsupported image size %d", im->nx);
+    }
+}
+
+int bioem_upload_score_twiddles(bioem_ctx* ctx) {
+    const int sizes[4] = {16, 32, 64, 128};
+    for (int k = 0; k < 4; ++k) {
+        const int M = sizes[k];
+        float2 h[128];
+        for (int t = 0; t < M; ++t) {
+            const double a = 2.0 * 3.14159265358979323846 * (double)t / (double)M;
+            h[t] = make_float2((float)cos(a), (float)sin(a));
+        }
+        cudaError_t e;
+        switch (M) {
+            case 16: e = cudaMemcpyToSymbol(c_w16, h, sizeof(float2) * 16); break;
+            case 32: e = cudaMemcpyToSymbol(c_w32, h, sizeof(float2) * 32); break;
+            case 64: e = cudaMemcpyToSymbol(c_w64, h, sizeof(float2) * 64); break;
+            default: e = cudaMemcpyToSymbol(c_w128, h, sizeof(float2) * 128); break;
+        }
+        if (e != cudaSuccess) return bioem_check_cuda(ctx, e, "twiddle upload");
+    }
+    return BIOEM_OK;
+}
