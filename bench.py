@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Throughput of the BioEM scoring hot path on GB300: parameter-set x image evaluations per second.
+
+One step = the whole path over one batch: prepare the images (moments + spectra), project the
+model for every parameter set (rotate, project, PSF), and score every image against every
+parameter set over every displacement (fused product / pruned inverse transform / likelihood /
+log-sum-exp) down to log P per image.
+
+Workload (per GPU): the "throughput" configuration — 2048 images of 128 x 128 px at 1.1 A, a
+5000-atom model, 36,864 Hopf-grid orientations x 4 defocus x 2 B-factors = 294,912 parameter
+sets, shifts within +-16 px (1089 displacements).  Images are synthesised on the GPU from the
+model through the library's synthetic-map entry point plus seeded shifts, normalisation, offset
+and noise.  Under torchrun every rank scores its own 2048 images against the full grid (weak
+scaling, no data-path collective).
+
+`--impl reference` times the FP64 CPU oracle instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+NCORES = os.cpu_count() or 1
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, str(NCORES))
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "parameter-set×image evals/sec (all shifts) at stated |Δlog P| vs FP64 oracle"
+UNIT = "evals/s"
+SCORE_SRC = os.path.join(ROOT, "paper_1609_06634_gb300", "csrc", "score.cu")
+
+# DRAM traffic of k_score from an ncu capture, valid only for the kernel source it was taken on.
+# bytes per evaluated pair at the throughput shape; None until a capture of the current source exists.
+K_SCORE_TRAFFIC = {"source_sha256": None, "bytes_per_pair": None}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="throughput")
+    ap.add_argument("--n-img", type=int, default=None, help="images per GPU (default: the workload's)")
+    ap.add_argument("--n-quat", type=int, default=None, help="use only the first n orientations (testing)")
+    ap.add_argument("--cpu-images", type=int, default=16, help="images in the CPU-oracle sample")
+    ap.add_argument("--cpu-quats", type=int, default=128, help="orientations in the CPU-oracle sample")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle leg")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def flops_per_eval(npix: int, max_shift: int) -> float:
+    """Algorithmic FP32 work of one (image, parameter set) evaluation over all shifts:
+    conjugate product 6 H + a full complex-to-real inverse FFT 2.5 n log2 n + the likelihood 4 S
+    (log1p and exp not counted)."""
+    n = npix * npix
+    h = npix * (npix // 2 + 1)
+    s = (2 * max_shift + 1) ** 2
+    return 6.0 * h + 2.5 * n * math.log2(n) + 4.0 * s
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms while running."""
+
+    FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.bus_id = bus_id
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return None
+        allrows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 10:
+                allrows.append(parts)
+        os.remove(self.path)
+        rows = [r for r in allrows if self.bus_id and self.bus_id.lower() in r[1].lower()] or allrows
+        if not rows:
+            return None
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[6 + k].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def synth_images(bioem, ctx, cfg, atoms_d, first: int, n: int):
+    """Observed images N I1(r + d) - mu + lambda z for images first..first+n of the workload."""
+    import torch
+    dev = ctx.device
+    truths = [workloads.image_truth(cfg, i) for i in range(first, first + n)]
+    quats = torch.from_numpy(np.stack([t["quat"] for t in truths]).astype(np.float32)).to(dev)
+    ctfs = [(t["defocus_A"], t["amp_contrast"], t["bfactor"], t["voltage_kV"]) for t in truths]
+    out = torch.empty((n, cfg.npix, cfg.npix), dtype=torch.float32, device=dev)
+    chunk = 1024
+    for c0 in range(0, n, chunk):
+        c1 = min(n, c0 + chunk)
+        maps = bioem.synthetic_maps(ctx, atoms_d, cfg.sigma_A, quats[c0:c1], ctfs[c0:c1], cfg.npix, cfg.pixel_A)
+        z = torch.from_numpy(np.stack([workloads.standard_normal_noise(cfg, first + i)
+                                       for i in range(c0, c1)]).astype(np.float32)).to(dev)
+        for k in range(c1 - c0):
+            t = truths[c0 + k]
+            sig = torch.roll(maps[k], shifts=(-t["dy"], -t["dx"]), dims=(0, 1)) * t["norm"]
+            lam = torch.sqrt(sig.double().var(unbiased=False) / cfg.snr).float()
+            out[c0 + k] = sig - t["offset"] + lam * z[k]
+    return out
+
+
+def run_cpu_oracle(images: np.ndarray, atoms, quats, ctfs, cfg):
+    import oracle
+    t0 = time.perf_counter()
+    r = oracle.score(images, atoms, quats, ctfs, cfg.sigma_A, cfg.pixel_A, cfg.max_shift)
+    dt = time.perf_counter() - t0
+    return r, dt
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def bench_reference(args):
+    """The FP64 oracle on the host cores, each step a bounded sample of the workload."""
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return 0
+    import oracle
+    cfg = workloads.get_config(args.workload)
+    n_img = max(1, min(4, args.cpu_images))
+    nq = max(1, min(64, args.cpu_quats))
+    wl = workloads.workload(cfg, n_img=n_img)
+    imgs = oracle.synthesize_images(wl)
+    quats = wl["quats"][:nq]
+    evals = n_img * nq * len(wl["ctfs"])
+    for _ in range(args.warmup):
+        run_cpu_oracle(imgs, wl["atoms"], quats, wl["ctfs"], cfg)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        run_cpu_oracle(imgs, wl["atoms"], quats, wl["ctfs"], cfg)
+    dt = (time.perf_counter() - t0) / max(1, args.steps)
+    value = evals / dt
+    sample = (f"{n_img} images x {nq} orientations x {len(wl['ctfs'])} PSFs x {cfg.n_shift} shifts of the "
+              f"{cfg.name} workload ({cfg.npix}x{cfg.npix} px); per step: projections, PSFs, direct-sum "
+              "correlations, closed-form likelihoods, log-sum-exp")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(cfg, n_img, len(quats) * len(wl["ctfs"])),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": NCORES, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(cfg, n_img, n_ps):
+    return {"workload": f"{cfg.name}: {n_img} images {cfg.npix}x{cfg.npix} px @ {cfg.pixel_A} A, {cfg.n_atoms}-atom "
+                        f"model, {n_ps} parameter sets ({cfg.orient} orientations x {cfg.n_defocus} defocus x "
+                        f"{len(cfg.bfactors)} B), shifts +-{cfg.max_shift} ({cfg.n_shift} per pair)",
+            "n_img": n_img, "n_ps": n_ps, "npix": cfg.npix, "max_shift": cfg.max_shift,
+            "l2": "inputs larger than L2 (projection spectra and image stack exceed the 126 MB L2)",
+            "step": "prepare_images + project_model + score"}
+
+
+def bench_ours(args):
+    import torch
+    import torch.distributed as tdist
+
+    import paper_1609_06634_gb300 as bioem
+    from paper_1609_06634_gb300 import build
+
+    world, rank, local = dist_setup(args)
+    if world > 1:
+        tdist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    cfg = workloads.get_config(args.workload)
+    n_img = args.n_img or cfg.n_img
+    wl = workloads.workload(cfg, n_img=0)
+    quats_np = wl["quats"] if args.n_quat is None else wl["quats"][:args.n_quat]
+    ctfs = wl["ctfs"]
+    n_ps = len(quats_np) * len(ctfs)
+
+    ctx = bioem.Context(local)
+    atoms_d = torch.from_numpy(wl["atoms"]).to(dev)
+    quats_d = torch.from_numpy(np.ascontiguousarray(quats_np)).to(dev)
+    images_d = synth_images(bioem, ctx, cfg, atoms_d, rank * n_img, n_img)
+    logp = torch.empty(n_img, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    if ctx.status() != 0:
+        raise RuntimeError("device status error during input synthesis")
+
+    def step(imgs, atoms, quats):
+        im = bioem.prepare_images(ctx, imgs, cfg.pixel_A)
+        ps = bioem.project_model(ctx, atoms, cfg.sigma_A, quats, ctfs, cfg.npix, cfg.pixel_A)
+        bioem.score(ctx, im, ps, cfg.max_shift, out=logp)
+        im.close()
+        ps.close()
+
+    def barrier():
+        if world > 1:
+            tdist.barrier()
+
+    for _ in range(args.warmup):
+        step(images_d, atoms_d, quats_d)
+    torch.cuda.synchronize()
+    if ctx.status() != 0:
+        raise RuntimeError("device status error in warm-up")
+
+    props = torch.cuda.get_device_properties(dev)
+    bus = getattr(props, "pci_bus_id", None)
+    bus_id = None
+    if bus is not None:
+        bus_id = f"{getattr(props, 'pci_domain_id', 0):08X}:{bus:02X}:{getattr(props, 'pci_device_id', 0):02X}"
+    stream = torch.cuda.current_stream(dev)
+    ctx.reset_kernel_stats()
+    ctx.set_kernel_timing(True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(bus_id) as clocks:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step(images_d, atoms_d, quats_d)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = ctx.launch_count()
+    k_ms, k_n = ctx.kernel_time("k_score")
+    kernel_ms = {name: ctx.kernel_time(name)[0] for name in
+                 ("k_prepare_images", "k_ctf_table", "k_project", "k_psf_spectra", "k_score", "k_reduce_wave",
+                  "k_finalize")}
+    ctx.set_kernel_timing(False)
+    if ctx.status() != 0:
+        raise RuntimeError("device status error in the timed steps")
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    evals = world * n_img * n_ps * args.steps
+    value = evals / (ms_max / 1e3)
+
+    # end to end through the public API: pinned host inputs in, log P out, copies inside the region
+    e2e = None
+    if not args.no_e2e:
+        img_h = images_d.cpu().pin_memory()
+        atoms_h = atoms_d.cpu().pin_memory()
+        quats_h = quats_d.cpu().pin_memory()
+        logp_h = torch.empty(n_img, dtype=torch.float64).pin_memory()
+
+        def e2e_step():
+            step(img_h.to(dev, non_blocking=True), atoms_h.to(dev, non_blocking=True),
+                 quats_h.to(dev, non_blocking=True))
+            logp_h.copy_(logp, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        te = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+        if world > 1:
+            tdist.all_reduce(te, op=tdist.ReduceOp.MAX)
+        h2d = img_h.numel() * 4 + atoms_h.numel() * 4 + quats_h.numel() * 4
+        e2e = {"value": evals / (float(te.item()) / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(n_img * 8)}
+
+    result = None
+    if rank == 0:
+        # roofline of the dominant kernel: FP32 ALU bound (pruned transforms + epilogue on CUDA cores)
+        fpe = flops_per_eval(cfg.npix, cfg.max_shift)
+        achieved = fpe * n_img * n_ps * args.steps / (k_ms / 1e3) / 1e12
+        clk = clocks.summary()
+        peak_mhz = 2070.0
+        try:
+            peak_mhz = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("sm_max_mhz", peak_mhz)
+        except (OSError, ValueError):
+            pass
+        peak = props.multi_processor_count * 128 * 2 * peak_mhz * 1e6 / 1e12
+        sha = hashlib.sha256(open(SCORE_SRC, "rb").read()).hexdigest()
+        traffic = None
+        if K_SCORE_TRAFFIC["source_sha256"] == sha and K_SCORE_TRAFFIC["bytes_per_pair"]:
+            traffic = K_SCORE_TRAFFIC["bytes_per_pair"] * n_img * n_ps / max(1, k_n / args.steps)
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "k_score",
+                "peak_basis": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes x 2 flop x {peak_mhz:.0f} MHz",
+                "flops_per_eval": fpe, "kernel_ms_per_step": k_ms / args.steps, "launches_per_step": k_n / args.steps}
+        if clk and clk.get("sm_mhz"):
+            roof["frac_at_observed_clock"] = achieved / (peak * clk["sm_mhz"] / peak_mhz)
+        result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                  "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                  "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                  "config": workload_config(cfg, n_img, n_ps), "roofline": roof, "e2e": e2e,
+                  "gpu_launches": int(launches), "clocks": clk,
+                  "kernel_ms_per_step": {k: v / args.steps for k, v in kernel_ms.items()}}
+
+        # CPU oracle on a bounded sample of the same workload, and the GPU's |d log P| on it
+        if not args.no_cpu:
+            ni = min(args.cpu_images, n_img)
+            nq = min(args.cpu_quats, len(quats_np))
+            sample_imgs = images_d[:ni].cpu().numpy()
+            ref, dt = run_cpu_oracle(sample_imgs, wl["atoms"], quats_np[:nq], ctfs, cfg)
+            im = bioem.prepare_images(ctx, images_d[:ni].contiguous(), cfg.pixel_A)
+            ps = bioem.project_model(ctx, atoms_d, cfg.sigma_A, quats_d[:nq].contiguous(), ctfs, cfg.npix, cfg.pixel_A)
+            got = bioem.score(ctx, im, ps, cfg.max_shift).cpu().numpy()
+            result["cpu_baseline"] = {
+                "value": ni * nq * len(ctfs) / dt, "unit": UNIT, "cores": NCORES, "kind": "oracle",
+                "sample": f"{ni} images x {nq} orientations x {len(ctfs)} PSFs x {cfg.n_shift} shifts of this "
+                          f"workload (the images the GPU scored); FP64 numpy oracle, {dt:.1f} s"}
+            result["dlogP_max_vs_oracle"] = float(np.max(np.abs(got - ref["logP"])))
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        tdist.barrier()
+        tdist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return bench_reference(args)
+    return bench_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

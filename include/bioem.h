@@ -144,6 +144,17 @@ int bioem_synthetic_maps(bioem_ctx* ctx, const float* d_atoms, int n_atoms, doub
                          const float* d_quats, const bioem_ctf* ctfs, int n, int nx, int ny,
                          double pixel_A, float* d_out);
 
+/* Measurement hooks.  bioem_launch_count: kernels the library has launched with this context
+ * since creation or the last reset.  With timing enabled, CUDA events are recorded on the
+ * context's stream around every launch; bioem_kernel_time synchronises the stream and returns the
+ * summed device time (ms) and the launch count of one kernel, by name: "k_prepare_images",
+ * "k_project", "k_ctf_table", "k_psf_spectra", "k_psf_real", "k_score", "k_reduce_wave",
+ * "k_finalize", "k_pairs_out".  bioem_reset_kernel_stats zeroes both. */
+int bioem_set_kernel_timing(bioem_ctx* ctx, int enable);
+int bioem_kernel_time(bioem_ctx* ctx, const char* kernel, double* total_ms, unsigned long long* launches);
+int bioem_reset_kernel_stats(bioem_ctx* ctx);
+unsigned long long bioem_launch_count(const bioem_ctx* ctx);
+
 /* Handle queries and release. */
 int bioem_images_count(const bioem_images* images);
 int bioem_projset_count(const bioem_projset* projset);

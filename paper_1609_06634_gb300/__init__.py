@@ -81,6 +81,24 @@ class Context:
     def set_scratch_limit(self, nbytes: int):
         _check(self, lib().bioem_set_scratch_limit(self._h, int(nbytes)), "set_scratch_limit")
 
+    def set_kernel_timing(self, on: bool = True):
+        """Record CUDA events on this context's stream around every library kernel launch."""
+        _check(self, lib().bioem_set_kernel_timing(self._h, 1 if on else 0), "set_kernel_timing")
+
+    def kernel_time(self, name: str) -> tuple[float, int]:
+        """(summed device ms, launches) of one library kernel since the last reset (synchronises)."""
+        ms = ctypes.c_double(0.0)
+        n = ctypes.c_ulonglong(0)
+        _check(self, lib().bioem_kernel_time(self._h, name.encode(), ctypes.byref(ms), ctypes.byref(n)), "kernel_time")
+        return ms.value, n.value
+
+    def reset_kernel_stats(self):
+        _check(self, lib().bioem_reset_kernel_stats(self._h), "reset_kernel_stats")
+
+    def launch_count(self) -> int:
+        """Kernels launched by the library with this context since creation or the last reset."""
+        return int(lib().bioem_launch_count(self._h))
+
     def status(self) -> int:
         """Synchronise the stream and read (and clear) the device status word."""
         out = ctypes.c_int(0)

@@ -36,6 +36,10 @@ SIGNATURES = {
     "bioem_score_pairs": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]),
     "bioem_synthetic_maps": (c_int, [c_void_p, c_void_p, c_int, c_double, c_void_p, ctypes.POINTER(CTF), c_int, c_int,
                                      c_int, c_double, c_void_p]),
+    "bioem_set_kernel_timing": (c_int, [c_void_p, c_int]),
+    "bioem_kernel_time": (c_int, [c_void_p, c_char_p, ctypes.POINTER(c_double), ctypes.POINTER(c_ull)]),
+    "bioem_reset_kernel_stats": (c_int, [c_void_p]),
+    "bioem_launch_count": (c_ull, [c_void_p]),
     "bioem_images_count": (c_int, [c_void_p]),
     "bioem_projset_count": (c_int, [c_void_p]),
     "bioem_free_images": (None, [c_void_p]),

@@ -5,6 +5,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <new>
+
 #include "bioem_internal.cuh"
 
 int bioem_set_error(bioem_ctx* ctx, int code, const char* fmt, ...) {
@@ -21,6 +23,43 @@ int bioem_check_cuda(bioem_ctx* ctx, cudaError_t e, const char* what) {
     if (e == cudaSuccess) return BIOEM_OK;
     if (e == cudaErrorMemoryAllocation) return bioem_set_error(ctx, BIOEM_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
     return bioem_set_error(ctx, BIOEM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+const char* const bioem_kernel_names[KID_COUNT] = {
+    "k_prepare_images", "k_project", "k_ctf_table", "k_psf_spectra", "k_psf_real",
+    "k_score", "k_reduce_wave", "k_finalize", "k_pairs_out"};
+
+void bioem_launch_begin(bioem_ctx* ctx, int kid) {
+    if (!ctx->timing) return;
+    bioem_timed_launch t{kid, nullptr, nullptr};
+    if (cudaEventCreate(&t.start) != cudaSuccess || cudaEventCreate(&t.stop) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    cudaEventRecord(t.start, ctx->stream);
+    ctx->pending.push_back(t);
+}
+
+void bioem_launch_end(bioem_ctx* ctx, int kid) {
+    ctx->n_launches++;
+    ctx->kid_launches[kid]++;
+    if (!ctx->timing || ctx->pending.empty() || ctx->pending.back().kid != kid || !ctx->pending.back().stop) return;
+    cudaEventRecord(ctx->pending.back().stop, ctx->stream);
+}
+
+// Fold the recorded event pairs into per-kernel totals (synchronises the stream).
+static int collect_timings(bioem_ctx* ctx) {
+    if (ctx->pending.empty()) return BIOEM_OK;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    for (auto& t : ctx->pending) {
+        float ms = 0.f;
+        if (e == cudaSuccess && cudaEventElapsedTime(&ms, t.start, t.stop) == cudaSuccess) ctx->kid_ms[t.kid] += ms;
+        cudaEventDestroy(t.start);
+        cudaEventDestroy(t.stop);
+    }
+    ctx->pending.clear();
+    cudaGetLastError();
+    return e == cudaSuccess ? BIOEM_OK : bioem_check_cuda(ctx, e, "timing synchronisation");
 }
 
 float2* bioem_twiddles(bioem_ctx* ctx, int npix) {
@@ -82,7 +121,7 @@ int bioem_create(bioem_ctx** out, int device, void* cuda_stream) {
         cudaGetLastError();
         return BIOEM_ERR_INVALID_ARG;
     }
-    bioem_ctx* ctx = (bioem_ctx*)calloc(1, sizeof(bioem_ctx));
+    bioem_ctx* ctx = new (std::nothrow) bioem_ctx();
     if (!ctx) return BIOEM_ERR_OOM;
     ctx->device = device;
     ctx->stream = (cudaStream_t)cuda_stream;
@@ -91,6 +130,16 @@ int bioem_create(bioem_ctx** out, int device, void* cuda_stream) {
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
         rc = BIOEM_ERR_CUDA;
+    }
+    if (!rc) {
+        // keep stream-ordered allocations cached in the device pool between calls instead of
+        // returning them to the driver at every synchronisation (projection sets are large)
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+            unsigned long long keep = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
     }
     if (!rc && cudaMalloc((void**)&ctx->d_status, sizeof(int)) != cudaSuccess) rc = BIOEM_ERR_OOM;
     if (!rc && cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess) rc = BIOEM_ERR_CUDA;
@@ -137,9 +186,46 @@ void bioem_destroy(bioem_ctx* ctx) {
     if (ctx->d_status) cudaFree(ctx->d_status);
     for (int k = 0; k < 5; ++k)
         if (ctx->d_tw[k]) cudaFree(ctx->d_tw[k]);
+    for (auto& t : ctx->pending) {
+        cudaEventDestroy(t.start);
+        cudaEventDestroy(t.stop);
+    }
     cudaGetLastError();
-    free(ctx);
+    delete ctx;
 }
+
+int bioem_set_kernel_timing(bioem_ctx* ctx, int enable) {
+    if (!ctx) return BIOEM_ERR_INVALID_ARG;
+    ctx->timing = enable ? 1 : 0;
+    return BIOEM_OK;
+}
+
+int bioem_kernel_time(bioem_ctx* ctx, const char* kernel, double* total_ms, unsigned long long* launches) {
+    if (!ctx || !kernel) return BIOEM_ERR_INVALID_ARG;
+    int kid = -1;
+    for (int k = 0; k < KID_COUNT; ++k)
+        if (strcmp(kernel, bioem_kernel_names[k]) == 0) kid = k;
+    if (kid < 0) return bioem_set_error(ctx, BIOEM_ERR_INVALID_ARG, "unknown kernel name %s", kernel);
+    cudaSetDevice(ctx->device);
+    const int rc = collect_timings(ctx);
+    if (total_ms) *total_ms = ctx->kid_ms[kid];
+    if (launches) *launches = ctx->kid_launches[kid];
+    return rc;
+}
+
+int bioem_reset_kernel_stats(bioem_ctx* ctx) {
+    if (!ctx) return BIOEM_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    const int rc = collect_timings(ctx);
+    ctx->n_launches = 0;
+    for (int k = 0; k < KID_COUNT; ++k) {
+        ctx->kid_launches[k] = 0;
+        ctx->kid_ms[k] = 0.0;
+    }
+    return rc;
+}
+
+unsigned long long bioem_launch_count(const bioem_ctx* ctx) { return ctx ? ctx->n_launches : 0ull; }
 
 int bioem_get_status(bioem_ctx* ctx, int* out_status) {
     if (!ctx || !out_status) return BIOEM_ERR_INVALID_ARG;

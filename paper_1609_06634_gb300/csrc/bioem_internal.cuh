@@ -4,7 +4,21 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/bioem.h"
+
+// ------------------------------------------------------------------ kernel accounting
+enum bioem_kernel_id {
+    KID_PREPARE = 0, KID_PROJECT, KID_CTF_TABLE, KID_PSF_SPECTRA, KID_PSF_REAL, KID_SCORE, KID_REDUCE_WAVE,
+    KID_FINALIZE, KID_PAIRS_OUT, KID_COUNT
+};
+extern const char* const bioem_kernel_names[KID_COUNT];
+
+struct bioem_timed_launch {
+    int kid;
+    cudaEvent_t start, stop;
+};
 
 // ------------------------------------------------------------------ handles
 struct bioem_ctx {
@@ -22,6 +36,12 @@ struct bioem_ctx {
     // twiddle tables (float2, W_N^k = exp(-2 pi i k / N)) for the direct transforms, by N
     float2* d_tw[5];
     char last_error[256];
+    // launch accounting and optional per-launch CUDA-event timing on the context's stream
+    unsigned long long n_launches;
+    unsigned long long kid_launches[KID_COUNT];
+    int timing;
+    std::vector<bioem_timed_launch> pending;
+    double kid_ms[KID_COUNT];
 };
 
 struct bioem_images {
@@ -98,6 +118,8 @@ int bioem_launch_score(bioem_ctx* ctx, const bioem_images* im, const bioem_projs
 int bioem_upload_score_twiddles(bioem_ctx* ctx);
 
 // abi.cu
+void bioem_launch_begin(bioem_ctx* ctx, int kid);   // call before a kernel launch
+void bioem_launch_end(bioem_ctx* ctx, int kid);     // call after it (counts it; records the stop event)
 int bioem_set_error(bioem_ctx* ctx, int code, const char* fmt, ...);
 int bioem_check_cuda(bioem_ctx* ctx, cudaError_t e, const char* what);
 float2* bioem_twiddles(bioem_ctx* ctx, int npix);

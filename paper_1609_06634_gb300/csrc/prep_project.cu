@@ -446,8 +446,10 @@ int build_ctf_table(bioem_ctx* ctx, const bioem_ctf* ctfs, int nctf, int npix, d
     e = cudaMemcpyAsync(d_coef, h, sizeof(double) * 3 * nctf, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) {
         const int blocks = (int)((tsize + 255) / 256 < 4096 ? (tsize + 255) / 256 : 4096);
+        bioem_launch_begin(ctx, KID_CTF_TABLE);
         k_ctf_table<<<blocks, 256, 0, ctx->stream>>>(d_coef, nctf, npix, pixel_A, *d_T);
         e = cudaGetLastError();
+        bioem_launch_end(ctx, KID_CTF_TABLE);
     }
     // the copy reads h asynchronously from pageable memory: it has completed once the call returns
     cudaFreeAsync(d_coef, ctx->stream);
@@ -465,8 +467,10 @@ int launch_prepare_n(bioem_ctx* ctx, const float* d_images, bioem_images* im) {
     const size_t sm = fwd_smem<N>();
     if (set_smem<N>((const void*)k_prepare_images<N>, sm)) return bioem_set_error(ctx, BIOEM_ERR_CUDA, "smem attribute");
     const double cn = bioem_log_norm_constant(N * N);
+    bioem_launch_begin(ctx, KID_PREPARE);
     k_prepare_images<N><<<im->n_img, kThreads, sm, ctx->stream>>>(d_images, bioem_twiddles(ctx, N), im->d_spec,
                                                                     im->d_nyq, im->d_kA, cn, ctx->d_status);
+    bioem_launch_end(ctx, KID_PREPARE);
     return bioem_check_cuda(ctx, cudaGetLastError(), "k_prepare_images");
 }
 
@@ -488,15 +492,19 @@ int launch_project_n(bioem_ctx* ctx, const float* d_atoms, int n_atoms, double s
     if (set_smem<N>((const void*)k_psf_spectra<N>, sm)) rc = bioem_set_error(ctx, BIOEM_ERR_CUDA, "smem attribute");
     for (int q0 = 0; q0 < nq && rc == BIOEM_OK; q0 += qw) {
         const int nb = nq - q0 < qw ? nq - q0 : qw;
+        bioem_launch_begin(ctx, KID_PROJECT);
         k_project<N><<<nb, kThreads, 0, ctx->stream>>>(reinterpret_cast<const float4*>(d_atoms), n_atoms,
                                                         reinterpret_cast<const float4*>(d_quats) + q0, sigma_A,
                                                         ps->pixel_A, d_I0);
+        bioem_launch_end(ctx, KID_PROJECT);
         rc = bioem_check_cuda(ctx, cudaGetLastError(), "k_project");
         if (rc) break;
         const size_t p0 = (size_t)q0 * nctf;
+        bioem_launch_begin(ctx, KID_PSF_SPECTRA);
         k_psf_spectra<N><<<nb, kThreads, sm, ctx->stream>>>(d_I0, bioem_twiddles(ctx, N), d_T, nctf,
                                                              ps->d_spec + p0 * N * (N / 2), ps->d_nyq + p0 * N,
                                                              ps->d_kB + p0, ctx->d_status);
+        bioem_launch_end(ctx, KID_PSF_SPECTRA);
         rc = bioem_check_cuda(ctx, cudaGetLastError(), "k_psf_spectra");
     }
     cudaFreeAsync(d_I0, ctx->stream);
@@ -515,13 +523,17 @@ int launch_synthetic_n(bioem_ctx* ctx, const float* d_atoms, int n_atoms, double
         cudaFreeAsync(d_T, ctx->stream);
         return bioem_set_error(ctx, BIOEM_ERR_OOM, "cudaMallocAsync(synthetic scratch)");
     }
+    bioem_launch_begin(ctx, KID_PROJECT);
     k_project<N><<<n, kThreads, 0, ctx->stream>>>(reinterpret_cast<const float4*>(d_atoms), n_atoms,
                                                    reinterpret_cast<const float4*>(d_quats), sigma_A, pixel_A, d_I0);
+    bioem_launch_end(ctx, KID_PROJECT);
     rc = bioem_check_cuda(ctx, cudaGetLastError(), "k_project");
     const size_t sm = fwd_smem<N>();
     if (!rc && set_smem<N>((const void*)k_psf_real<N>, sm)) rc = bioem_set_error(ctx, BIOEM_ERR_CUDA, "smem attribute");
     if (!rc) {
+        bioem_launch_begin(ctx, KID_PSF_REAL);
         k_psf_real<N><<<n, kThreads, sm, ctx->stream>>>(d_I0, bioem_twiddles(ctx, N), d_T, d_out);
+        bioem_launch_end(ctx, KID_PSF_REAL);
         rc = bioem_check_cuda(ctx, cudaGetLastError(), "k_psf_real");
     }
     cudaFreeAsync(d_I0, ctx->stream);

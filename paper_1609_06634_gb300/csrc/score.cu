@@ -549,29 +549,37 @@ int run_score(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, i
         const long long n_items = n_chunks * n_img;
         if (n_items > 0x7fffffffll) return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE, "too many work items");
         const int grid = (int)(n_items < slots ? n_items : slots);
+        bioem_launch_begin(ctx, KID_SCORE);
         k_score<C><<<grid, C::THREADS, smem, ctx->stream>>>(im->d_spec, im->d_nyq, n_img, ps->d_spec, ps->d_nyq, wbegin,
                                                              wl, (int)chunk, (int)n_items, max_shift, c1f, rec_t, rec_s,
                                                              rec_d, ctx->d_status);
+        bioem_launch_end(ctx, KID_SCORE);
         int rc = bioem_check_cuda(ctx, cudaGetLastError(), "k_score");
         if (rc) return rc;
         if (pairs_mode) {
+            bioem_launch_begin(ctx, KID_PAIRS_OUT);
             k_pairs_out<<<1024, 256, 0, ctx->stream>>>(rec_t, rec_s, im->d_kA, ps->d_kB, n_img, wbegin, wl, c1,
                                                        out.pair_max, out.pair_lse, range_len, (int)w0);
+            bioem_launch_end(ctx, KID_PAIRS_OUT);
         } else {
             const double log_norm_orient = log((double)nctf * S);
+            bioem_launch_begin(ctx, KID_REDUCE_WAVE);
             k_reduce_wave<<<n_img, kRedThreads, 0, ctx->stream>>>(rec_t, rec_s, rec_d, im->d_kA, ps->d_kB, wbegin, wl,
                                                                   nctf, ps->nq, c1, log_norm_orient,
                                                                   reinterpret_cast<Acc*>(ctx->d_acc), w0 == 0,
                                                                   out.logP_orient);
+            bioem_launch_end(ctx, KID_REDUCE_WAVE);
         }
         rc = bioem_check_cuda(ctx, cudaGetLastError(), "reduction");
         if (rc) return rc;
     }
     if (!pairs_mode) {
         const double log_norm = log((double)ps->n_ps * S);
+        bioem_launch_begin(ctx, KID_FINALIZE);
         k_finalize<<<(n_img + 255) / 256, 256, 0, ctx->stream>>>(reinterpret_cast<const Acc*>(ctx->d_acc), n_img, log_norm,
                                                                   nctf, nsk, C::SMAX, out.logP, out.best_q, out.best_ctf,
                                                                   out.best_dx, out.best_dy, out.best_logL);
+        bioem_launch_end(ctx, KID_FINALIZE);
         return bioem_check_cuda(ctx, cudaGetLastError(), "k_finalize");
     }
     return BIOEM_OK;
