@@ -255,8 +255,7 @@ int bioem_prepare_images(bioem_ctx* ctx, const float* d_images, int n_img, int n
     im->nx = nx;
     im->ny = ny;
     im->pixel_A = pixel_A;
-    int rc = alloc(ctx, &im->d_spec, (size_t)n_img * ny * (nx / 2), "image spectra");
-    if (!rc) rc = alloc(ctx, &im->d_nyq, (size_t)n_img * ny, "image spectra");
+    int rc = alloc(ctx, &im->d_spec, (size_t)n_img * ny * (nx / 2 + 1), "image spectra");
     if (!rc) rc = alloc(ctx, &im->d_kA, (size_t)n_img, "image constants");
     if (!rc && n_img > 0) rc = bioem_launch_prepare(ctx, d_images, im);
     if (rc) {
@@ -294,8 +293,7 @@ int bioem_project_model(bioem_ctx* ctx, const float* d_atoms, int n_atoms, doubl
     ps->nx = nx;
     ps->ny = ny;
     ps->pixel_A = pixel_A;
-    int rc = alloc(ctx, &ps->d_spec, (size_t)ps->n_ps * ny * (nx / 2), "projection spectra");
-    if (!rc) rc = alloc(ctx, &ps->d_nyq, (size_t)ps->n_ps * ny, "projection spectra");
+    int rc = alloc(ctx, &ps->d_spec, (size_t)ps->n_ps * ny * (nx / 2 + 1), "projection spectra");
     if (!rc) rc = alloc(ctx, &ps->d_kB, (size_t)ps->n_ps, "projection constants");
     if (!rc && nq > 0) rc = bioem_launch_project(ctx, d_atoms, n_atoms, sigma_A, d_quats, nq, ctfs, nctf, ps);
     if (rc) {
@@ -389,7 +387,6 @@ void bioem_free_images(bioem_images* im) {
     if (!im) return;
     cudaSetDevice(im->ctx->device);
     release(im->ctx, im->d_spec);
-    release(im->ctx, im->d_nyq);
     release(im->ctx, im->d_kA);
     free(im);
 }
@@ -398,7 +395,6 @@ void bioem_free_projset(bioem_projset* ps) {
     if (!ps) return;
     cudaSetDevice(ps->ctx->device);
     release(ps->ctx, ps->d_spec);
-    release(ps->ctx, ps->d_nyq);
     release(ps->ctx, ps->d_kB);
     free(ps);
 }

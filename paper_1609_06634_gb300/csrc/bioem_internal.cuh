@@ -48,8 +48,7 @@ struct bioem_images {
     bioem_ctx* ctx;
     int n_img, nx, ny;
     double pixel_A;
-    float2* d_spec;   // [n_img][ny][nx/2] unit-norm half spectrum (kx < nx/2), DC = 0
-    float2* d_nyq;    // [n_img][ny] Nyquist column kx = nx/2
+    float2* d_spec;   // [n_img][ny][nx/2 + 1] unit-norm half spectrum, DC = 0
     double* d_kA;     // [n_img] (3-n)/2 ln A + c(n)
 };
 
@@ -57,8 +56,7 @@ struct bioem_projset {
     bioem_ctx* ctx;
     int nq, nctf, n_ps, nx, ny;
     double pixel_A;
-    float2* d_spec;   // [n_ps][ny][nx/2] unit-norm PSF-filtered projection spectrum, DC = 0
-    float2* d_nyq;    // [n_ps][ny]
+    float2* d_spec;   // [n_ps][ny][nx/2 + 1] unit-norm PSF-filtered projection spectrum, DC = 0
     double* d_kB;     // [n_ps] -1/2 ln B
 };
 

@@ -115,19 +115,17 @@ __device__ void load_twiddles(const float2* __restrict__ g_tw, float2* tw) {
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = g_tw[i];
 }
 
-// Write F * scale (DC zeroed) to a [N][N/2] main block and the [N] Nyquist column.
+// Write F * T * scale (DC zeroed) to a [N][N/2 + 1] half spectrum.
 template <int N>
 __device__ void store_half_spectrum(const float2* F, const float* __restrict__ T, float scale,
-                                    float2* __restrict__ spec, float2* __restrict__ nyq) {
-    constexpr int H = N / 2 + 1, NC = N / 2;
+                                    float2* __restrict__ spec) {
+    constexpr int H = N / 2 + 1;
     for (int o = threadIdx.x; o < N * H; o += blockDim.x) {
-        const int ky = o / H, kx = o - ky * H;
         float2 v = F[o];
         if (T) v = c_scale(v, T[o]);
         v = c_scale(v, scale);
         if (o == 0) v = make_float2(0.f, 0.f);
-        if (kx < NC) spec[ky * NC + kx] = v;
-        else nyq[ky] = v;
+        spec[o] = v;
     }
 }
 
@@ -153,7 +151,6 @@ template <int N>
 __global__ void __launch_bounds__(kThreads) k_prepare_images(const float* __restrict__ images,
                                                               const float2* __restrict__ g_tw,
                                                               float2* __restrict__ spec,
-                                                              float2* __restrict__ nyq,
                                                               double* __restrict__ kA, double cn,
                                                               int* __restrict__ status) {
     constexpr int H = N / 2 + 1;
@@ -182,7 +179,7 @@ __global__ void __launch_bounds__(kThreads) k_prepare_images(const float* __rest
     const double e = half_spectrum_energy<N>(F, nullptr, red);
     const bool bad = !(A > 0.0) || !(e > 0.0);
     const float scale = bad ? 0.f : (float)(1.0 / sqrt(e));
-    store_half_spectrum<N>(F, nullptr, scale, spec + (size_t)w * N * (N / 2), nyq + (size_t)w * N);
+    store_half_spectrum<N>(F, nullptr, scale, spec + (size_t)w * N * H);
     if (threadIdx.x == 0) {
         if (bad) {
             atomicOr(status, BIOEM_DEV_NUMERIC);
@@ -340,7 +337,6 @@ __global__ void __launch_bounds__(kThreads) k_psf_spectra(const float* __restric
                                                            const float2* __restrict__ g_tw,
                                                            const float* __restrict__ T, int nctf,
                                                            float2* __restrict__ spec,
-                                                           float2* __restrict__ nyq,
                                                            double* __restrict__ kB,
                                                            int* __restrict__ status) {
     constexpr int H = N / 2 + 1;
@@ -359,7 +355,7 @@ __global__ void __launch_bounds__(kThreads) k_psf_spectra(const float* __restric
         const double B = half_spectrum_energy<N>(F, Tc, red);   // n C_cc - C_c^2 (Plancherel)
         const bool bad = !(B > 0.0);
         const size_t p = (size_t)q * nctf + c;
-        store_half_spectrum<N>(F, Tc, bad ? 0.f : (float)(1.0 / sqrt(B)), spec + p * N * (N / 2), nyq + p * N);
+        store_half_spectrum<N>(F, Tc, bad ? 0.f : (float)(1.0 / sqrt(B)), spec + p * N * H);
         if (threadIdx.x == 0) {
             if (bad) {
                 atomicOr(status, BIOEM_DEV_NUMERIC);
@@ -469,7 +465,7 @@ int launch_prepare_n(bioem_ctx* ctx, const float* d_images, bioem_images* im) {
     const double cn = bioem_log_norm_constant(N * N);
     bioem_launch_begin(ctx, KID_PREPARE);
     k_prepare_images<N><<<im->n_img, kThreads, sm, ctx->stream>>>(d_images, bioem_twiddles(ctx, N), im->d_spec,
-                                                                    im->d_nyq, im->d_kA, cn, ctx->d_status);
+                                                                    im->d_kA, cn, ctx->d_status);
     bioem_launch_end(ctx, KID_PREPARE);
     return bioem_check_cuda(ctx, cudaGetLastError(), "k_prepare_images");
 }
@@ -502,8 +498,8 @@ int launch_project_n(bioem_ctx* ctx, const float* d_atoms, int n_atoms, double s
         const size_t p0 = (size_t)q0 * nctf;
         bioem_launch_begin(ctx, KID_PSF_SPECTRA);
         k_psf_spectra<N><<<nb, kThreads, sm, ctx->stream>>>(d_I0, bioem_twiddles(ctx, N), d_T, nctf,
-                                                             ps->d_spec + p0 * N * (N / 2), ps->d_nyq + p0 * N,
-                                                             ps->d_kB + p0, ctx->d_status);
+                                                             ps->d_spec + p0 * N * (N / 2 + 1), ps->d_kB + p0,
+                                                             ctx->d_status);
         bioem_launch_end(ctx, KID_PSF_SPECTRA);
         rc = bioem_check_cuda(ctx, cudaGetLastError(), "k_psf_spectra");
     }

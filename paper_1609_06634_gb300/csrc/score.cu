@@ -111,92 +111,82 @@ struct Cfg {
     static constexpr int SMAX = SMAX_;
     static constexpr int PB = PB_;             // pairs per batch
     static constexpr int NC = N / 2;
-    static constexpr int NCOL = NC + 1;        // stage-A columns per pair (kx = 0..N/2)
+    static constexpr int H = NC + 1;           // half-spectrum row length (kx = 0..N/2)
     static constexpr int NS = 2 * SMAX + 1;    // displacements per axis
     static constexpr int NROW = 2 * SMAX;      // stage-B transform rows per pair (dy < SMAX)
-    static constexpr int THREADS = PB * NROW;
     static constexpr int R = N / L;            // sub-sequences per transform
-    static constexpr int QS = NCOL;            // Q row stride (complex); odd -> conflict-free columns
-    static constexpr int TASKS_A = PB * NCOL;
+    static constexpr int TASKS_A = PB * H;     // stage-A column tasks per batch
+    static constexpr int KA = PB * NC / 256;   // stage-A tasks per thread
+    static constexpr int THREADS = TASKS_A / KA;
+    static_assert(PB * NROW == 256, "one stage-B row per thread of the first 256");
+    static_assert(TASKS_A % KA == 0 && THREADS >= 256, "balanced stage A");
+    static constexpr int QS = H;               // Q row stride (complex); odd -> conflict-free columns
     static constexpr int NDIR = PB * NS;       // outputs of the dy = +SMAX row, evaluated directly
-    static constexpr size_t SM_IMG = (size_t)N * NC * sizeof(float2);
-    static constexpr size_t SM_NYQ = (size_t)N * sizeof(float2);
+    static constexpr size_t SM_IMG = (size_t)N * H * sizeof(float2);
     static constexpr size_t SM_Q = (size_t)PB * NS * QS * sizeof(float2);
     static constexpr size_t SM_TW = (size_t)N * sizeof(float2);
+    static constexpr size_t SM_TWC = (size_t)R * NS * sizeof(float2);
     static constexpr size_t SM_ROW = (size_t)PB * NROW * (2 * sizeof(float) + sizeof(int));
     static constexpr size_t SM_DIR = (size_t)NDIR * sizeof(float);
-    static constexpr size_t SMEM = SM_IMG + SM_NYQ + SM_Q + SM_TW + SM_ROW + SM_DIR;
+    static constexpr size_t SMEM = SM_IMG + SM_Q + SM_TW + SM_TWC + SM_ROW + SM_DIR;
 };
 
-// acc[mi] += W_N^(b m) y[m mod L] for m = mi - SMAX (complex accumulate)
-template <int N, int SMAX, int B, int MI>
-__device__ __forceinline__ void combine_complex(float2 (&acc)[2 * SMAX + 1], const float2 (&x)[L]) {
-    if constexpr (MI < 2 * SMAX + 1) {
-        constexpr int m = MI - SMAX;
-        constexpr int u = bitrev(pmod(m, L), ilog2(L));
-        constexpr int t = pmod(B * m, N);
-        if constexpr (t == 0) {
-            acc[MI] = c_add(acc[MI], x[u]);
-        } else {
-            const float2 w = cw<N>(t);
-            acc[MI].x = fmaf(w.x, x[u].x, fmaf(-w.y, x[u].y, acc[MI].x));
-            acc[MI].y = fmaf(w.x, x[u].y, fmaf(w.y, x[u].x, acc[MI].y));
-        }
-        combine_complex<N, SMAX, B, MI + 1>(acc, x);
-    }
-}
-
-// acc[mi] += Re(W_N^(b m) y[m mod L])
-template <int N, int SMAX, int B, int MI>
-__device__ __forceinline__ void combine_real(float (&acc)[2 * SMAX + 1], const float2 (&x)[L]) {
-    if constexpr (MI < 2 * SMAX + 1) {
-        constexpr int m = MI - SMAX;
-        constexpr int u = bitrev(pmod(m, L), ilog2(L));
-        constexpr int t = pmod(B * m, N);
-        if constexpr (t == 0) {
-            acc[MI] += x[u].x;
-        } else {
-            const float2 w = cw<N>(t);
-            acc[MI] = fmaf(w.x, x[u].x, fmaf(-w.y, x[u].y, acc[MI]));
-        }
-        combine_real<N, SMAX, B, MI + 1>(acc, x);
-    }
-}
-
-// Stage A for one column: sub-sequences b = 0..R-1 (rows ky = b + R a).
-template <class C, int B>
-__device__ __forceinline__ void stage_a_sub(float2 (&acc)[C::NS], const float2* __restrict__ img_col,
-                                            const float2* __restrict__ ps_col, int stride) {
-    if constexpr (B < C::R) {
+// Stage A for one column kx of one pair: Q(dy, kx) for dy = -SMAX..SMAX, with the rows ky = b + R a
+// of sub-sequence b transformed by an in-register FFT and recombined with the twiddles
+// twc[b][m] = W_N^(b (m - SMAX)) (shared memory, the same address for every thread: broadcast).
+// The projection column is read from global memory one sub-sequence ahead of its use.
+template <class C>
+__device__ __forceinline__ void stage_a_column(float2 (&acc)[C::NS], const float2* __restrict__ img_col,
+                                               const float2* __restrict__ ps_col, const float2* __restrict__ twc) {
+    constexpr int H = C::H, R = C::R, NS = C::NS, SMAX = C::SMAX;
+    float2 cn[L];
+#pragma unroll
+    for (int a = 0; a < L; ++a) cn[a] = __ldg(ps_col + (R * a) * H);
+#pragma unroll 1
+    for (int b = 0; b < R; ++b) {
         float2 x[L];
 #pragma unroll
-        for (int a = 0; a < L; ++a) {
-            const int ky = B + C::R * a;
-            const float2 o = img_col[ky * stride];
-            const float2 c = __ldg(ps_col + ky * stride);
-            x[a] = c_mulc(o, c);
+        for (int a = 0; a < L; ++a) x[a] = c_mulc(img_col[(R * a) * H], cn[a]);
+        if (b + 1 < R) {
+#pragma unroll
+            for (int a = 0; a < L; ++a) cn[a] = __ldg(ps_col + (R * a + 1) * H);
         }
+        img_col += H;
+        ps_col += H;
         fft_dif<L>(x);
-        combine_complex<C::N, C::SMAX, B, 0>(acc, x);
-        stage_a_sub<C, B + 1>(acc, img_col, ps_col, stride);
+        const float2* tw = twc + b * NS;
+#pragma unroll
+        for (int mi = 0; mi < NS; ++mi) {
+            const int u = bitrev(pmod(mi - SMAX, L), ilog2(L));
+            const float2 w = tw[mi];
+            acc[mi].x = fmaf(w.x, x[u].x, fmaf(-w.y, x[u].y, acc[mi].x));
+            acc[mi].y = fmaf(w.x, x[u].y, fmaf(w.y, x[u].x, acc[mi].y));
+        }
     }
 }
 
-// Stage B for one row: inputs R(kx) = w_kx Q(dy, kx) for kx < N/2 (kx = b + R a).
-template <class C, int B>
-__device__ __forceinline__ void stage_b_sub(float (&acc)[C::NS], const float2* __restrict__ qrow) {
-    if constexpr (B < C::R) {
+// Stage B for one row: rho-part(dx) = Re sum_{kx < N/2} w_kx Q(dy, kx) W_N^(kx dx), kx = b + R a;
+// only a < L/2 carries data (kx < N/2 for every b < R).
+template <class C>
+__device__ __forceinline__ void stage_b_row(float (&acc)[C::NS], const float2* __restrict__ qrow,
+                                            const float2* __restrict__ twc) {
+    constexpr int R = C::R, NS = C::NS, SMAX = C::SMAX;
+#pragma unroll 1
+    for (int b = 0; b < R; ++b) {
         float2 x[L];
 #pragma unroll
-        for (int a = 0; a < L; ++a) {
-            const int kx = B + C::R * a;
-            if (kx == 0) x[a] = make_float2(qrow[0].x, 0.f);
-            else if (kx < C::NC) x[a] = c_scale(qrow[kx], 2.f);
-            else x[a] = make_float2(0.f, 0.f);
-        }
+        for (int a = 0; a < L / 2; ++a) x[a] = c_scale(qrow[b + R * a], 2.f);
+        if (b == 0) x[0] = make_float2(qrow[0].x, 0.f);   // kx = 0: weight 1, real
+#pragma unroll
+        for (int a = L / 2; a < L; ++a) x[a] = make_float2(0.f, 0.f);
         fft_dif<L>(x);
-        combine_real<C::N, C::SMAX, B, 0>(acc, x);
-        stage_b_sub<C, B + 1>(acc, qrow);
+        const float2* tw = twc + b * NS;
+#pragma unroll
+        for (int mi = 0; mi < NS; ++mi) {
+            const int u = bitrev(pmod(mi - SMAX, L), ilog2(L));
+            const float2 w = tw[mi];
+            acc[mi] = fmaf(w.x, x[u].x, fmaf(-w.y, x[u].y, acc[mi]));
+        }
     }
 }
 
@@ -232,17 +222,16 @@ __device__ __forceinline__ float loglik_t(float rho, int* status) {
 
 template <class C>
 __global__ void __launch_bounds__(C::THREADS, 1)
-k_score(const float2* __restrict__ img_spec, const float2* __restrict__ img_nyq, int n_img,
-        const float2* __restrict__ ps_spec, const float2* __restrict__ ps_nyq, int ps_begin, int ps_count,
-        int chunk, int n_items, int s, float c1, float* __restrict__ rec_t, float* __restrict__ rec_s,
+k_score(const float2* __restrict__ img_spec, int n_img, const float2* __restrict__ ps_spec, int ps_begin,
+        int ps_count, int chunk, int n_items, int s, float c1, float* __restrict__ rec_t, float* __restrict__ rec_s,
         int* __restrict__ rec_d, int* __restrict__ status) {
-    constexpr int N = C::N, NC = C::NC, NS = C::NS, SMAX = C::SMAX, NROW = C::NROW;
+    constexpr int N = C::N, NC = C::NC, H = C::H, NS = C::NS, SMAX = C::SMAX, NROW = C::NROW;
     extern __shared__ __align__(16) unsigned char smem[];
     float2* img_s = reinterpret_cast<float2*>(smem);
-    float2* nyq_s = reinterpret_cast<float2*>(smem + C::SM_IMG);
-    float2* q_s = reinterpret_cast<float2*>(smem + C::SM_IMG + C::SM_NYQ);
-    float2* tw_s = reinterpret_cast<float2*>(smem + C::SM_IMG + C::SM_NYQ + C::SM_Q);
-    float* row_t = reinterpret_cast<float*>(smem + C::SM_IMG + C::SM_NYQ + C::SM_Q + C::SM_TW);
+    float2* q_s = reinterpret_cast<float2*>(smem + C::SM_IMG);
+    float2* tw_s = reinterpret_cast<float2*>(smem + C::SM_IMG + C::SM_Q);
+    float2* twc_s = tw_s + N;
+    float* row_t = reinterpret_cast<float*>(twc_s + C::R * NS);
     float* row_s = row_t + C::PB * NROW;
     int* row_d = reinterpret_cast<int*>(row_s + C::PB * NROW);
     float* dir_t = reinterpret_cast<float*>(row_d + C::PB * NROW);
@@ -250,7 +239,12 @@ k_score(const float2* __restrict__ img_spec, const float2* __restrict__ img_nyq,
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     constexpr int NWARPS = (C::THREADS + 31) / 32;
-    for (int i = tid; i < N; i += C::THREADS) tw_s[i] = cw_table<N>()[i];
+    const float2* cwN = cw_table<N>();
+    for (int i = tid; i < N; i += C::THREADS) tw_s[i] = cwN[i];
+    for (int i = tid; i < C::R * NS; i += C::THREADS) {
+        const int b = i / NS, m = i - (i / NS) * NS - SMAX;
+        twc_s[i] = cwN[pmod(b * m, N)];
+    }
 
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int ci = item / n_img;
@@ -259,41 +253,38 @@ k_score(const float2* __restrict__ img_spec, const float2* __restrict__ img_nyq,
         const int hi = min(lo + chunk, ps_count);
         __syncthreads();   // previous item's readers of img_s are done
         {
-            const float4* src = reinterpret_cast<const float4*>(img_spec + (size_t)w * N * NC);
+            const float4* src = reinterpret_cast<const float4*>(img_spec + (size_t)w * N * H);
             float4* dst = reinterpret_cast<float4*>(img_s);
-            for (int i = tid; i < N * NC / 2; i += C::THREADS) dst[i] = __ldg(src + i);
-            for (int i = tid; i < N; i += C::THREADS) nyq_s[i] = img_nyq[(size_t)w * N + i];
+            for (int i = tid; i < N * H / 2; i += C::THREADS) dst[i] = __ldg(src + i);
         }
         __syncthreads();
         for (int p0 = lo; p0 < hi; p0 += C::PB) {
-            // ---------------- stage A: one column of one pair per task
-            for (int task = tid; task < C::TASKS_A; task += C::THREADS) {
-                const int j = task / C::NCOL;
-                const int kx = task - j * C::NCOL;
+            // ---------------- stage A: one column of one pair per task, KA tasks per thread
+#pragma unroll 1
+            for (int k = 0; k < C::KA; ++k) {
+                const int task = tid + k * C::THREADS;
+                const int j = task / H;
+                const int kx = task - j * H;
                 const int p = min(p0 + j, hi - 1);
-                const size_t gp = (size_t)(ps_begin + p);
-                const bool nyq = (kx == NC);
-                const float2* img_col = nyq ? nyq_s : img_s + kx;
-                const float2* ps_col = nyq ? ps_nyq + gp * N : ps_spec + gp * N * NC + kx;
-                const int stride = nyq ? 1 : NC;
+                const float2* ps_col = ps_spec + (size_t)(ps_begin + p) * N * H + kx;
                 float2 acc[NS];
 #pragma unroll
                 for (int m = 0; m < NS; ++m) acc[m] = make_float2(0.f, 0.f);
-                stage_a_sub<C, 0>(acc, img_col, ps_col, stride);
+                stage_a_column<C>(acc, img_s + kx, ps_col, twc_s);
                 float2* qdst = q_s + (size_t)j * NS * C::QS + kx;
 #pragma unroll
                 for (int m = 0; m < NS; ++m) qdst[m * C::QS] = acc[m];
             }
             __syncthreads();
             // ---------------- stage B: one row (dy = -SMAX .. SMAX-1) of one pair per thread
-            {
+            if (tid < C::PB * NROW) {
                 const int j = tid / NROW;
                 const int r = tid - j * NROW;
                 const float2* qrow = q_s + ((size_t)j * NS + r) * C::QS;
                 float acc[NS];
 #pragma unroll
                 for (int m = 0; m < NS; ++m) acc[m] = 0.f;
-                stage_b_sub<C, 0>(acc, qrow);
+                stage_b_row<C>(acc, qrow, twc_s);
                 const float qn = qrow[NC].x;   // Nyquist column, weight 1, phase (-1)^dx
                 const bool row_ok = abs(r - SMAX) <= s;
                 float tmin = INFINITY;
@@ -342,7 +333,8 @@ k_score(const float2* __restrict__ img_spec, const float2* __restrict__ img_nyq,
                 const int p = p0 + j;
                 if (p >= hi) continue;
                 Part acc{INFINITY, 0.f, 0x7fffffff};
-                for (int r = lane; r < NROW; r += 32) acc = merge(acc, Part{row_t[j * NROW + r], row_s[j * NROW + r], row_d[j * NROW + r]}, c1);
+                for (int r = lane; r < NROW; r += 32)
+                    acc = merge(acc, Part{row_t[j * NROW + r], row_s[j * NROW + r], row_d[j * NROW + r]}, c1);
                 for (int mi = lane; mi < NS; mi += 32) {
                     const float t = dir_t[j * NS + mi];
                     acc = merge(acc, Part{t, t < INFINITY ? 1.f : 0.f, 2 * SMAX * NS + mi}, c1);
@@ -550,9 +542,9 @@ int run_score(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, i
         if (n_items > 0x7fffffffll) return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE, "too many work items");
         const int grid = (int)(n_items < slots ? n_items : slots);
         bioem_launch_begin(ctx, KID_SCORE);
-        k_score<C><<<grid, C::THREADS, smem, ctx->stream>>>(im->d_spec, im->d_nyq, n_img, ps->d_spec, ps->d_nyq, wbegin,
-                                                             wl, (int)chunk, (int)n_items, max_shift, c1f, rec_t, rec_s,
-                                                             rec_d, ctx->d_status);
+        k_score<C><<<grid, C::THREADS, smem, ctx->stream>>>(im->d_spec, n_img, ps->d_spec, wbegin, wl, (int)chunk,
+                                                             (int)n_items, max_shift, c1f, rec_t, rec_s, rec_d,
+                                                             ctx->d_status);
         bioem_launch_end(ctx, KID_SCORE);
         int rc = bioem_check_cuda(ctx, cudaGetLastError(), "k_score");
         if (rc) return rc;
