@@ -90,8 +90,8 @@ int alloc(bioem_ctx* ctx, T** p, size_t count, const char* what) {
     return BIOEM_OK;
 }
 
-void release(bioem_ctx* ctx, void* p) {
-    if (p) cudaFreeAsync(p, ctx->stream);
+void release(cudaStream_t stream, void* p) {
+    if (p) cudaFreeAsync(p, stream);
 }
 
 }  // namespace
@@ -251,6 +251,8 @@ int bioem_prepare_images(bioem_ctx* ctx, const float* d_images, int n_img, int n
     bioem_images* im = (bioem_images*)calloc(1, sizeof(bioem_images));
     if (!im) return BIOEM_ERR_OOM;
     im->ctx = ctx;
+    im->device = ctx->device;
+    im->stream = ctx->stream;
     im->n_img = n_img;
     im->nx = nx;
     im->ny = ny;
@@ -287,6 +289,8 @@ int bioem_project_model(bioem_ctx* ctx, const float* d_atoms, int n_atoms, doubl
     bioem_projset* ps = (bioem_projset*)calloc(1, sizeof(bioem_projset));
     if (!ps) return BIOEM_ERR_OOM;
     ps->ctx = ctx;
+    ps->device = ctx->device;
+    ps->stream = ctx->stream;
     ps->nq = nq;
     ps->nctf = nctf;
     ps->n_ps = nq * nctf;
@@ -385,17 +389,17 @@ int bioem_projset_count(const bioem_projset* projset) { return projset ? projset
 
 void bioem_free_images(bioem_images* im) {
     if (!im) return;
-    cudaSetDevice(im->ctx->device);
-    release(im->ctx, im->d_spec);
-    release(im->ctx, im->d_kA);
+    cudaSetDevice(im->device);
+    release(im->stream, im->d_spec);
+    release(im->stream, im->d_kA);
     free(im);
 }
 
 void bioem_free_projset(bioem_projset* ps) {
     if (!ps) return;
-    cudaSetDevice(ps->ctx->device);
-    release(ps->ctx, ps->d_spec);
-    release(ps->ctx, ps->d_kB);
+    cudaSetDevice(ps->device);
+    release(ps->stream, ps->d_spec);
+    release(ps->stream, ps->d_kB);
     free(ps);
 }
 

@@ -45,7 +45,9 @@ struct bioem_ctx {
 };
 
 struct bioem_images {
-    bioem_ctx* ctx;
+    bioem_ctx* ctx;          // creating context (compared, never dereferenced after it is destroyed)
+    int device;              // handles free their memory with their own device and stream
+    cudaStream_t stream;
     int n_img, nx, ny;
     double pixel_A;
     float2* d_spec;   // [n_img][ny][nx/2 + 1] unit-norm half spectrum, DC = 0
@@ -54,6 +56,8 @@ struct bioem_images {
 
 struct bioem_projset {
     bioem_ctx* ctx;
+    int device;
+    cudaStream_t stream;
     int nq, nctf, n_ps, nx, ny;
     double pixel_A;
     float2* d_spec;   // [n_ps][ny][nx/2 + 1] unit-norm PSF-filtered projection spectrum, DC = 0

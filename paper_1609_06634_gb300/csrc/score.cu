@@ -238,7 +238,7 @@ k_score(const float2* __restrict__ img_spec, int n_img, const float2* __restrict
 
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    constexpr int NWARPS = (C::THREADS + 31) / 32;
+    constexpr int NWARPS = C::THREADS / 32;   // full warps only: the last warp may be partial
     const float2* cwN = cw_table<N>();
     for (int i = tid; i < N; i += C::THREADS) tw_s[i] = cwN[i];
     for (int i = tid; i < C::R * NS; i += C::THREADS) {
@@ -328,8 +328,8 @@ k_score(const float2* __restrict__ img_spec, int n_img, const float2* __restrict
                 dir_t[i] = ok ? loglik_t(rho, status) : INFINITY;
             }
             __syncthreads();
-            // ---------------- combine the pieces of each pair (one warp per pair)
-            for (int j = warp; j < C::PB; j += NWARPS) {
+            // ---------------- combine the pieces of each pair (one full warp per pair)
+            for (int j = warp; warp < NWARPS && j < C::PB; j += NWARPS) {
                 const int p = p0 + j;
                 if (p >= hi) continue;
                 Part acc{INFINITY, 0.f, 0x7fffffff};
