@@ -144,6 +144,26 @@ int bioem_synthetic_maps(bioem_ctx* ctx, const float* d_atoms, int n_atoms, doub
                          const float* d_quats, const bioem_ctf* ctfs, int n, int nx, int ny,
                          double pixel_A, float* d_out);
 
+/* Scoring that allocates no device memory.  The paper has no counterpart: this is an addition of
+ * this library for callers that may not allocate at scoring time, for example a service whose
+ * device memory is reserved up front by another allocator (an extra cudaMalloc could fail or
+ * fragment that reservation), or a latency-sensitive loop where cudaMalloc / cudaFree would
+ * stall on device synchronisation.  Prepare the images and the parameter sets beforehand.
+ * Computes exactly what bioem_score computes with d_logP_per_orient = NULL, into d_logP
+ * [n_img] float64 device.  Its scratch (per-image accumulators and per-pair records) is one
+ * 16 MiB array that the library reserves statically on every GPU it is loaded on, until the
+ * process exits; parameter sets are processed in as many passes as that array requires.
+ *   Limit: n_img * (32 + 12 * nctf) bytes, rounded up to 256, must fit in 16 MiB, else
+ *          BIOEM_ERR_UNSUPPORTED_SIZE with the sizes in bioem_last_error().
+ *   The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *   that device current; make that first call before any stream capture.
+ *   Every call uses the same array and leaves its contents behind (each call initialises what it
+ *   reads).  Calls whose work overlaps on the GPU (other streams, other host threads or
+ *   contexts) race on the array and corrupt each other's results: serialise them.
+ * Other errors as bioem_score. */
+int bioem_score_noalloc(bioem_ctx* ctx, const bioem_images* images, const bioem_projset* projset,
+                        int max_shift, double* d_logP);
+
 /* Measurement hooks.  bioem_launch_count: kernels the library has launched with this context
  * since creation or the last reset.  With timing enabled, CUDA events are recorded on the
  * context's stream around every launch; bioem_kernel_time synchronises the stream and returns the

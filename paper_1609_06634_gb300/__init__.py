@@ -15,7 +15,7 @@ from . import _native
 from ._native import CTF
 
 __all__ = ["BioEMError", "Context", "Images", "ProjSet", "prepare_images", "project_model", "score", "score_all",
-           "best_params", "score_pairs", "synthetic_maps", "ctf_array", "lib"]
+           "best_params", "score_pairs", "score_noalloc", "synthetic_maps", "ctf_array", "lib"]
 
 OK = 0
 ERR_INVALID_ARG, ERR_UNSUPPORTED_SIZE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NUMERIC = -1, -2, -3, -4, -5, -6
@@ -200,6 +200,20 @@ def score(ctx: Context, images: Images, projset: ProjSet, max_shift: int, out=No
         out = torch.empty(images.n_img, dtype=torch.float64, device=ctx.device)
     _check(ctx, lib().bioem_score(ctx._h, images._h, projset._h, int(max_shift), _ptr(out), ctypes.c_void_p(0)),
            "score")
+    return out
+
+
+def score_noalloc(ctx: Context, images: Images, projset: ProjSet, max_shift: int, out):
+    """bioem_score_noalloc: log P into the caller's [n_img] float64 device tensor ``out``.
+
+    The library allocates no device memory in this call (its scratch is a fixed 16 MiB array
+    reserved when the library is loaded), for callers that must not allocate while scoring.
+    """
+    torch = _torch()
+    t = _dev_tensor(out, torch.float64, ctx.device, "out", ndim=1)
+    if t.data_ptr() != out.data_ptr() or t.shape[0] != images.n_img:
+        raise BioEMError(ERR_INVALID_ARG, "out must be a contiguous [n_img] float64 tensor")
+    _check(ctx, lib().bioem_score_noalloc(ctx._h, images._h, projset._h, int(max_shift), _ptr(out)), "score_noalloc")
     return out
 
 

@@ -33,6 +33,7 @@ SIGNATURES = {
                                   c_void_p]),
     "bioem_score_all": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p,
                                 c_void_p, c_void_p, c_void_p]),
+    "bioem_score_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     "bioem_score_pairs": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]),
     "bioem_synthetic_maps": (c_int, [c_void_p, c_void_p, c_int, c_double, c_void_p, ctypes.POINTER(CTF), c_int, c_int,
                                      c_int, c_double, c_void_p]),

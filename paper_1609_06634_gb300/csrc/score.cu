@@ -22,6 +22,8 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <mutex>
+
 #include "bioem_internal.cuh"
 
 namespace {
@@ -626,4 +628,129 @@ int bioem_upload_score_twiddles(bioem_ctx* ctx) {
         if (e != cudaSuccess) return bioem_check_cuda(ctx, e, "twiddle upload");
     }
     return BIOEM_OK;
+}
+
+// ---------------------------------------------------------------------------- allocation-free scoring
+// Scratch for bioem_score_noalloc: per-image accumulators followed by per-pair records, reserved
+// statically in device memory on every GPU this library is loaded on, for the life of the process.
+// Host code must not use the symbol's host-side address: each device's address is looked up once
+// with cudaGetSymbolAddress while that device is current.
+
+namespace {
+
+constexpr size_t kNoAllocBytes = 16u << 20;   // 16 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the static scratch on the current device (looked up on first use).
+int noalloc_scratch(bioem_ctx* ctx, void** out) {
+    if (ctx->device < 0 || ctx->device >= kMaxDevices)
+        return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE, "device ordinal %d too large", ctx->device);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[ctx->device]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return bioem_check_cuda(ctx, e != cudaSuccess ? e : cudaErrorInvalidSymbol,
+                                                             "cudaGetSymbolAddress(static scoring scratch)");
+        g_noalloc_ptr[ctx->device] = p;
+    }
+    *out = g_noalloc_ptr[ctx->device];
+    return BIOEM_OK;
+}
+
+// The wave loop of bioem_score (log P only) with records and accumulators in the static scratch.
+template <class C>
+int run_score_noalloc(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, int max_shift, double* logP) {
+    const int n_img = im->n_img;
+    const int nctf = ps->nctf;
+    if (n_img == 0) return BIOEM_OK;
+    const size_t acc_bytes = ((sizeof(Acc) * (size_t)n_img + 255) / 256) * 256;
+    const size_t per_ps = (size_t)n_img * 12;
+    if (acc_bytes + per_ps * nctf > kNoAllocBytes)
+        return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE,
+                               "allocation-free scoring: %d images x %d PSFs need %zu bytes of scratch, more than "
+                               "the static %zu", n_img, nctf, acc_bytes + per_ps * nctf, kNoAllocBytes);
+    void* base = nullptr;
+    int rc = noalloc_scratch(ctx, &base);
+    if (rc) return rc;
+    long long wave = (long long)((kNoAllocBytes - acc_bytes) / per_ps);
+    wave -= wave % nctf;
+    if (wave > ps->n_ps) wave = ps->n_ps;
+    Acc* acc = reinterpret_cast<Acc*>(base);
+    float* rec_t = reinterpret_cast<float*>(static_cast<unsigned char*>(base) + acc_bytes);
+    float* rec_s = rec_t + (size_t)n_img * wave;
+    int* rec_d = reinterpret_cast<int*>(rec_s + (size_t)n_img * wave);
+
+    const size_t smem = C::SMEM;
+    if (cudaFuncSetAttribute(k_score<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return bioem_set_error(ctx, BIOEM_ERR_CUDA, "shared memory attribute (%zu bytes)", smem);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score<C>, C::THREADS, smem) != cudaSuccess || per_sm < 1)
+        return bioem_set_error(ctx, BIOEM_ERR_CUDA, "occupancy query");
+    const int slots = per_sm * ctx->num_sms;
+    const int n = C::N * C::N;
+    const float c1f = 0.5f * (3.0f - (float)n);
+    const double c1 = 0.5 * (3.0 - (double)n);
+    const int S = (2 * max_shift + 1) * (2 * max_shift + 1);
+    for (long long w0 = 0; w0 < ps->n_ps; w0 += wave) {
+        const int wl = (int)(ps->n_ps - w0 < wave ? ps->n_ps - w0 : wave);
+        const long long per_img = (4ll * slots + n_img - 1) / n_img;
+        long long chunk = (wl + per_img - 1) / per_img;
+        chunk = ((chunk + C::PB - 1) / C::PB) * C::PB;
+        if (chunk > 512) chunk = 512;
+        if (chunk < C::PB) chunk = C::PB;
+        const long long n_items = ((wl + chunk - 1) / chunk) * n_img;
+        if (n_items > 0x7fffffffll) return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE, "too many work items");
+        const int grid = (int)(n_items < slots ? n_items : slots);
+        k_score<C><<<grid, C::THREADS, smem, ctx->stream>>>(im->d_spec, n_img, ps->d_spec, (int)w0, wl, (int)chunk,
+                                                             (int)n_items, max_shift, c1f, rec_t, rec_s, rec_d,
+                                                             ctx->d_status);
+        ctx->n_launches++;
+        ctx->kid_launches[KID_SCORE]++;
+        rc = bioem_check_cuda(ctx, cudaGetLastError(), "k_score");
+        if (rc) return rc;
+        k_reduce_wave<<<n_img, kRedThreads, 0, ctx->stream>>>(rec_t, rec_s, rec_d, im->d_kA, ps->d_kB, (int)w0, wl,
+                                                              nctf, ps->nq, c1, log((double)nctf * S), acc, w0 == 0,
+                                                              nullptr);
+        ctx->n_launches++;
+        ctx->kid_launches[KID_REDUCE_WAVE]++;
+        rc = bioem_check_cuda(ctx, cudaGetLastError(), "k_reduce_wave");
+        if (rc) return rc;
+    }
+    k_finalize<<<(n_img + 255) / 256, 256, 0, ctx->stream>>>(acc, n_img, log((double)ps->n_ps * S), nctf, C::NS,
+                                                              C::SMAX, logP, nullptr, nullptr, nullptr, nullptr,
+                                                              nullptr);
+    ctx->n_launches++;
+    ctx->kid_launches[KID_FINALIZE]++;
+    return bioem_check_cuda(ctx, cudaGetLastError(), "k_finalize");
+}
+
+}  // namespace
+
+extern "C" int bioem_score_noalloc(bioem_ctx* ctx, const bioem_images* images, const bioem_projset* projset,
+                                   int max_shift, double* d_logP) {
+    if (!ctx || !images || !projset) return BIOEM_ERR_INVALID_ARG;
+    if (images->ctx != ctx || projset->ctx != ctx)
+        return bioem_set_error(ctx, BIOEM_ERR_INVALID_ARG, "handle from another context");
+    if (images->nx != projset->nx || images->ny != projset->ny ||
+        fabs(images->pixel_A - projset->pixel_A) > 1e-9 * images->pixel_A)
+        return bioem_set_error(ctx, BIOEM_ERR_INVALID_ARG, "images and projections differ in size or pixel");
+    if (max_shift < 0) return bioem_set_error(ctx, BIOEM_ERR_INVALID_ARG, "negative max_shift");
+    if (!bioem_score_supported(images->nx, max_shift))
+        return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE, "max_shift %d unsupported at %d px", max_shift,
+                               images->nx);
+    if (projset->n_ps == 0) return bioem_set_error(ctx, BIOEM_ERR_INVALID_ARG, "empty parameter set");
+    if (images->n_img > 0 && !d_logP) return bioem_set_error(ctx, BIOEM_ERR_INVALID_ARG, "d_logP is required");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return bioem_set_error(ctx, BIOEM_ERR_CUDA, "cudaSetDevice");
+    switch (images->nx) {
+        case 32: return run_score_noalloc<C32_4>(ctx, images, projset, max_shift, d_logP);
+        case 64: return max_shift <= 4 ? run_score_noalloc<C64_4>(ctx, images, projset, max_shift, d_logP)
+                                       : run_score_noalloc<C64_8>(ctx, images, projset, max_shift, d_logP);
+        case 128: return max_shift <= 4 ? run_score_noalloc<C128_4>(ctx, images, projset, max_shift, d_logP)
+                                        : run_score_noalloc<C128_16>(ctx, images, projset, max_shift, d_logP);
+        default: return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE, "unsupported image size %d", images->nx);
+    }
 }
