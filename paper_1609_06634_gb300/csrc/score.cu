@@ -107,7 +107,7 @@ __host__ __device__ constexpr int bitrev(int u, int bits) {
 __host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
 __host__ __device__ constexpr int pmod(int a, int m) { return ((a % m) + m) % m; }
 
-template <int N_, int SMAX_, int PB_, int THREADS_>
+template <int N_, int SMAX_, int PB_>
 struct Cfg {
     static constexpr int N = N_;
     static constexpr int SMAX = SMAX_;
@@ -115,33 +115,44 @@ struct Cfg {
     static constexpr int NC = N / 2;
     static constexpr int H = NC + 1;           // half-spectrum row length (kx = 0..N/2)
     static constexpr int NS = 2 * SMAX + 1;    // displacements per axis
+    static constexpr int NROW = 2 * SMAX;      // stage-B transform rows per pair (dy < SMAX)
     static constexpr int R = N / L;            // sub-sequences per transform
-    static constexpr int TASKS_A = PB * H;     // stage A: one column of one pair per task
-    static constexpr int UNITS_B = PB * NS * 2;  // stage B: one half (R/2 sub-sequences) of one row per unit
-    static constexpr int THREADS = THREADS_;
-    static constexpr int NWARPS = THREADS / 32;  // full warps (the last warp may be partial)
-    static_assert(R % 2 == 0, "stage B splits the sub-sequences in two halves");
-    static_assert(THREADS >= 256 && THREADS <= 1024, "block size");
+    static constexpr int TASKS_A = PB * H;     // stage-A column tasks per batch
+    static constexpr int KA = PB * NC / 256;   // stage-A tasks per thread
+    static constexpr int THREADS = TASKS_A / KA;
+    static_assert(PB * NROW == 256, "one stage-B row per thread of the first 256");
+    static_assert(TASKS_A % KA == 0 && THREADS >= 256, "balanced stage A");
     static constexpr int QS = H;               // Q row stride (complex); odd -> conflict-free columns
+    static constexpr int NDIR = PB * NS;       // outputs of the dy = +SMAX row, evaluated directly
     static constexpr size_t SM_IMG = (size_t)N * H * sizeof(float2);
     static constexpr size_t SM_Q = (size_t)PB * NS * QS * sizeof(float2);
+    static constexpr size_t SM_TW = (size_t)N * sizeof(float2);
     static constexpr size_t SM_TWC = (size_t)R * NS * sizeof(float2);
-    static constexpr size_t SM_PART = (size_t)UNITS_B * (2 * sizeof(float) + sizeof(int));
-    static constexpr size_t SMEM = SM_IMG + SM_Q + SM_TWC + SM_PART;
+    static constexpr size_t SM_ROW = (size_t)PB * NROW * (2 * sizeof(float) + sizeof(int));
+    static constexpr size_t SM_DIR = (size_t)NDIR * sizeof(float);
+    static constexpr size_t SMEM = SM_IMG + SM_Q + SM_TW + SM_TWC + SM_ROW + SM_DIR;
 };
 
 // Stage A for one column kx of one pair: Q(dy, kx) for dy = -SMAX..SMAX, with the rows ky = b + R a
 // of sub-sequence b transformed by an in-register FFT and recombined with the twiddles
 // twc[b][m] = W_N^(b (m - SMAX)) (shared memory, the same address for every thread: broadcast).
+// The projection column is read from global memory one sub-sequence ahead of its use.
 template <class C>
 __device__ __forceinline__ void stage_a_column(float2 (&acc)[C::NS], const float2* __restrict__ img_col,
                                                const float2* __restrict__ ps_col, const float2* __restrict__ twc) {
     constexpr int H = C::H, R = C::R, NS = C::NS, SMAX = C::SMAX;
+    float2 cn[L];
+#pragma unroll
+    for (int a = 0; a < L; ++a) cn[a] = __ldg(ps_col + (R * a) * H);
 #pragma unroll 1
     for (int b = 0; b < R; ++b) {
         float2 x[L];
 #pragma unroll
-        for (int a = 0; a < L; ++a) x[a] = c_mulc(img_col[(R * a) * H], __ldg(ps_col + (R * a) * H));
+        for (int a = 0; a < L; ++a) x[a] = c_mulc(img_col[(R * a) * H], cn[a]);
+        if (b + 1 < R) {
+#pragma unroll
+            for (int a = 0; a < L; ++a) cn[a] = __ldg(ps_col + (R * a + 1) * H);
+        }
         img_col += H;
         ps_col += H;
         fft_dif<L>(x);
@@ -156,14 +167,14 @@ __device__ __forceinline__ void stage_a_column(float2 (&acc)[C::NS], const float
     }
 }
 
-// Stage B, half h of one row: partial Re sum over kx = b + R a (b in [h R/2, (h+1) R/2)) of
-// w_kx Q(dy, kx) W_N^(kx dx); only a < L/2 carries data (kx < N/2 for every b < R).
+// Stage B for one row: rho-part(dx) = Re sum_{kx < N/2} w_kx Q(dy, kx) W_N^(kx dx), kx = b + R a;
+// only a < L/2 carries data (kx < N/2 for every b < R).
 template <class C>
-__device__ __forceinline__ void stage_b_half(float (&acc)[C::NS], const float2* __restrict__ qrow, int h,
-                                             const float2* __restrict__ twc) {
+__device__ __forceinline__ void stage_b_row(float (&acc)[C::NS], const float2* __restrict__ qrow,
+                                            const float2* __restrict__ twc) {
     constexpr int R = C::R, NS = C::NS, SMAX = C::SMAX;
 #pragma unroll 1
-    for (int b = h * (R / 2); b < (h + 1) * (R / 2); ++b) {
+    for (int b = 0; b < R; ++b) {
         float2 x[L];
 #pragma unroll
         for (int a = 0; a < L / 2; ++a) x[a] = c_scale(qrow[b + R * a], 2.f);
@@ -216,19 +227,22 @@ __global__ void __launch_bounds__(C::THREADS, 1)
 k_score(const float2* __restrict__ img_spec, int n_img, const float2* __restrict__ ps_spec, int ps_begin,
         int ps_count, int chunk, int n_items, int s, float c1, float* __restrict__ rec_t, float* __restrict__ rec_s,
         int* __restrict__ rec_d, int* __restrict__ status) {
-    constexpr int N = C::N, NC = C::NC, H = C::H, NS = C::NS, SMAX = C::SMAX;
-    constexpr int NE = (NS + 1) / 2;   // outputs per stage-B half-thread after the exchange
+    constexpr int N = C::N, NC = C::NC, H = C::H, NS = C::NS, SMAX = C::SMAX, NROW = C::NROW;
     extern __shared__ __align__(16) unsigned char smem[];
     float2* img_s = reinterpret_cast<float2*>(smem);
     float2* q_s = reinterpret_cast<float2*>(smem + C::SM_IMG);
-    float2* twc_s = reinterpret_cast<float2*>(smem + C::SM_IMG + C::SM_Q);
-    float* part_t = reinterpret_cast<float*>(twc_s + C::R * NS);
-    float* part_s = part_t + C::UNITS_B;
-    int* part_d = reinterpret_cast<int*>(part_s + C::UNITS_B);
+    float2* tw_s = reinterpret_cast<float2*>(smem + C::SM_IMG + C::SM_Q);
+    float2* twc_s = tw_s + N;
+    float* row_t = reinterpret_cast<float*>(twc_s + C::R * NS);
+    float* row_s = row_t + C::PB * NROW;
+    int* row_d = reinterpret_cast<int*>(row_s + C::PB * NROW);
+    float* dir_t = reinterpret_cast<float*>(row_d + C::PB * NROW);
 
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
+    constexpr int NWARPS = C::THREADS / 32;   // full warps only: the last warp may be partial
     const float2* cwN = cw_table<N>();
+    for (int i = tid; i < N; i += C::THREADS) tw_s[i] = cwN[i];
     for (int i = tid; i < C::R * NS; i += C::THREADS) {
         const int b = i / NS, m = i - (i / NS) * NS - SMAX;
         twc_s[i] = cwN[pmod(b * m, N)];
@@ -247,9 +261,10 @@ k_score(const float2* __restrict__ img_spec, int n_img, const float2* __restrict
         }
         __syncthreads();
         for (int p0 = lo; p0 < hi; p0 += C::PB) {
-            // ---------------- stage A: one column of one pair per task
+            // ---------------- stage A: one column of one pair per task, KA tasks per thread
 #pragma unroll 1
-            for (int task = tid; task < C::TASKS_A; task += C::THREADS) {
+            for (int k = 0; k < C::KA; ++k) {
+                const int task = tid + k * C::THREADS;
                 const int j = task / H;
                 const int kx = task - j * H;
                 const int p = min(p0 + j, hi - 1);
@@ -263,58 +278,71 @@ k_score(const float2* __restrict__ img_spec, int n_img, const float2* __restrict
                 for (int m = 0; m < NS; ++m) qdst[m * C::QS] = acc[m];
             }
             __syncthreads();
-            // ---------------- stage B: half a row per unit; the two halves of a row are adjacent lanes
-#pragma unroll 1
-            for (int unit = tid; unit < C::UNITS_B; unit += C::THREADS) {
-                const int j = unit / (2 * NS);
-                const int r = (unit >> 1) - j * NS;   // row: dy = r - SMAX
-                const int h = unit & 1;
+            // ---------------- stage B: one row (dy = -SMAX .. SMAX-1) of one pair per thread
+            if (tid < C::PB * NROW) {
+                const int j = tid / NROW;
+                const int r = tid - j * NROW;
                 const float2* qrow = q_s + ((size_t)j * NS + r) * C::QS;
                 float acc[NS];
 #pragma unroll
                 for (int m = 0; m < NS; ++m) acc[m] = 0.f;
-                stage_b_half<C>(acc, qrow, h, twc_s);
-                // exchange partial sums with the other half (lane ^ 1); this lane keeps dx index 2k + h
-                float mine[NE];
-#pragma unroll
-                for (int k = 0; k < NE; ++k) {
-                    const float s0 = acc[2 * k] + __shfl_xor_sync(0xffffffffu, acc[2 * k], 1);
-                    float s1 = 0.f;
-                    if (2 * k + 1 < NS) s1 = acc[2 * k + 1] + __shfl_xor_sync(0xffffffffu, acc[2 * k + 1], 1);
-                    mine[k] = h ? s1 : s0;
-                }
-                const float qn = qrow[NC].x;                        // Nyquist column, weight 1
-                const float nyq = ((h - SMAX) & 1) ? -qn : qn;      // phase (-1)^dx, dx = 2k + h - SMAX
+                stage_b_row<C>(acc, qrow, twc_s);
+                const float qn = qrow[NC].x;   // Nyquist column, weight 1, phase (-1)^dx
                 const bool row_ok = abs(r - SMAX) <= s;
                 float tmin = INFINITY;
                 int arg = 0x7fffffff;
 #pragma unroll
-                for (int k = 0; k < NE; ++k) {
-                    const int mi = 2 * k + h;
-                    const bool ok = row_ok && mi < NS && abs(mi - SMAX) <= s;
-                    const float t = ok ? loglik_t(mine[k] + nyq, status) : INFINITY;
-                    mine[k] = t;
+                for (int m = 0; m < NS; ++m) {
+                    const float rho = acc[m] + (((m - SMAX) & 1) ? -qn : qn);
+                    const bool ok = row_ok && abs(m - SMAX) <= s;
+                    const float t = ok ? loglik_t(rho, status) : INFINITY;
+                    acc[m] = t;
                     if (t < tmin) {
                         tmin = t;
-                        arg = r * NS + mi;
+                        arg = r * NS + m;
                     }
                 }
                 float ssum = 0.f;
 #pragma unroll
-                for (int k = 0; k < NE; ++k) ssum += (mine[k] < INFINITY) ? __expf(c1 * (mine[k] - tmin)) : 0.f;
-                part_t[unit] = tmin;
-                part_s[unit] = ssum;
-                part_d[unit] = arg;
+                for (int m = 0; m < NS; ++m) ssum += (acc[m] < INFINITY) ? __expf(c1 * (acc[m] - tmin)) : 0.f;
+                row_t[tid] = tmin;
+                row_s[tid] = ssum;
+                row_d[tid] = arg;
+            }
+            // ---------------- the dy = +SMAX row, one output per task, evaluated directly; the
+            // threads without a stage-B row (tid >= PB NROW) take the first outputs so that no
+            // thread with a row gets two
+#pragma unroll 1
+            for (int i = (tid + C::THREADS - C::PB * NROW) % C::THREADS; i < C::NDIR; i += C::THREADS) {
+                const int j = i / NS;
+                const int mi = i - j * NS;
+                const int dx = mi - SMAX;
+                const float2* qrow = q_s + ((size_t)j * NS + 2 * SMAX) * C::QS;
+                float accv = 0.f;
+                int idx = pmod(dx, N);
+                const int step = idx;
+                for (int kx = 1; kx < NC; ++kx) {
+                    const float2 v = qrow[kx];
+                    const float2 wv = tw_s[idx];
+                    accv = fmaf(v.x, wv.x, fmaf(-v.y, wv.y, accv));
+                    idx += step;
+                    idx -= (idx >= N) ? N : 0;
+                }
+                const float rho = qrow[0].x + 2.f * accv + ((dx & 1) ? -qrow[NC].x : qrow[NC].x);
+                const bool ok = SMAX <= s && abs(dx) <= s;
+                dir_t[i] = ok ? loglik_t(rho, status) : INFINITY;
             }
             __syncthreads();
-            // ---------------- combine the 2 NS pieces of each pair (one full warp per pair)
-            for (int j = warp; warp < C::NWARPS && j < C::PB; j += C::NWARPS) {
+            // ---------------- combine the pieces of each pair (one full warp per pair)
+            for (int j = warp; warp < NWARPS && j < C::PB; j += NWARPS) {
                 const int p = p0 + j;
                 if (p >= hi) continue;
                 Part acc{INFINITY, 0.f, 0x7fffffff};
-                for (int q = lane; q < 2 * NS; q += 32) {
-                    const int u = j * 2 * NS + q;
-                    acc = merge(acc, Part{part_t[u], part_s[u], part_d[u]}, c1);
+                for (int r = lane; r < NROW; r += 32)
+                    acc = merge(acc, Part{row_t[j * NROW + r], row_s[j * NROW + r], row_d[j * NROW + r]}, c1);
+                for (int mi = lane; mi < NS; mi += 32) {
+                    const float t = dir_t[j * NS + mi];
+                    acc = merge(acc, Part{t, t < INFINITY ? 1.f : 0.f, 2 * SMAX * NS + mi}, c1);
                 }
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) {
@@ -554,13 +582,11 @@ int run_score(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, i
     return BIOEM_OK;
 }
 
-// <N, SMAX, pairs per batch, threads>: threads cover the stage-B half-rows (2 PB (2 SMAX + 1)) and,
-// where possible, the stage-A columns (PB (N/2 + 1)) in one round.
-using C32_4 = Cfg<32, 4, 32, 576>;
-using C64_4 = Cfg<64, 4, 16, 528>;
-using C64_8 = Cfg<64, 8, 16, 544>;
-using C128_4 = Cfg<128, 4, 16, 520>;
-using C128_16 = Cfg<128, 16, 8, 528>;
+using C32_4 = Cfg<32, 4, 32>;
+using C64_4 = Cfg<64, 4, 32>;
+using C64_8 = Cfg<64, 8, 16>;
+using C128_4 = Cfg<128, 4, 32>;
+using C128_16 = Cfg<128, 16, 8>;
 
 }  // namespace
 
