@@ -39,6 +39,7 @@ extern "C" {
 typedef struct bioem_ctx bioem_ctx;
 typedef struct bioem_images bioem_images;
 typedef struct bioem_projset bioem_projset;
+typedef struct bioem_batch bioem_batch;
 
 /* One point of the PSF grid, in physical units (the CTF and envelope after Eq. 4).
  * Converted to the paper's coefficients as a = lambda_e * defocus_A / (2 pi),
@@ -163,6 +164,32 @@ int bioem_synthetic_maps(bioem_ctx* ctx, const float* d_atoms, int n_atoms, doub
  * Other errors as bioem_score. */
 int bioem_score_noalloc(bioem_ctx* ctx, const bioem_images* images, const bioem_projset* projset,
                         int max_shift, double* d_logP);
+
+/* Batched scoring of several models against several image stacks of mixed sizes (the paper's
+ * ensemble setting of Eq. 10 needs P_mw for every model m and image w; Sec. 4 scores large image
+ * sets against a model).  A segment is one (model m, stack k) pair: stacks[k] (prepared images of
+ * 64, 96, 128 or 192 px) against projsets[m * n_stacks + k] (model m projected for stack k's size,
+ * pixel and grid) with |d| <= max_shift[k] (at most N/8).  bioem_batch_create builds the work list
+ * of all segments, allocates the per-pair records (12 bytes per pair of every segment) and captures
+ * one persistent scoring launch plus one reduction launch in a CUDA graph; bioem_batch_run replays
+ * the graph on the context's stream.  Output: d_logP_matrix [n_models][sum_k n_img_k] float32,
+ * ln P(image | model) as bioem_score computes it, images of stack k in columns
+ * [sum_{k'<k} n_img_k', ...).  Handles must outlive the batch.  Work items use the chunk size
+ * chosen by bioem_autotune for their (size, shift window), or a default.
+ * Errors: INVALID_ARG, UNSUPPORTED_SIZE, OOM, CUDA. */
+int bioem_batch_create(bioem_ctx* ctx, int n_models, int n_stacks, const bioem_images* const* stacks,
+                       const bioem_projset* const* projsets, const int* max_shift, float* d_logP_matrix,
+                       bioem_batch** out);
+int bioem_batch_run(bioem_batch* batch);
+long long bioem_batch_evals(const bioem_batch* batch);   /* image x parameter-set pairs per run */
+void bioem_batch_free(bioem_batch* batch);
+
+/* Tile autotuner for the batched launch: times candidate chunk sizes (parameter sets per work
+ * item) on a trial slice of (images, projset) and keeps the fastest for (image size, max_shift)
+ * in this process; with cache_path it first reads, and afterwards rewrites, a text file of
+ * "npix shift chunk" lines.  *out_chunk (may be NULL) receives the choice. */
+int bioem_autotune(bioem_ctx* ctx, const bioem_images* images, const bioem_projset* projset, int max_shift,
+                   const char* cache_path, int* out_chunk);
 
 /* Measurement hooks.  bioem_launch_count: kernels the library has launched with this context
  * since creation or the last reset.  With timing enabled, CUDA events are recorded on the

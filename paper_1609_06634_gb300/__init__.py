@@ -15,7 +15,7 @@ from . import _native
 from ._native import CTF
 
 __all__ = ["BioEMError", "Context", "Images", "ProjSet", "prepare_images", "project_model", "score", "score_all",
-           "best_params", "score_pairs", "score_noalloc", "synthetic_maps", "ctf_array", "lib"]
+           "best_params", "score_pairs", "score_noalloc", "Batch", "autotune", "synthetic_maps", "ctf_array", "lib"]
 
 OK = 0
 ERR_INVALID_ARG, ERR_UNSUPPORTED_SIZE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NUMERIC = -1, -2, -3, -4, -5, -6
@@ -238,6 +238,58 @@ def score_pairs(ctx: Context, images: Images, projset: ProjSet, max_shift: int, 
     _check(ctx, lib().bioem_score_pairs(ctx._h, images._h, projset._h, int(max_shift), int(ps_begin), int(ps_count),
                                         _ptr(pmax), _ptr(plse)), "score_pairs")
     return pmax, plse
+
+
+class Batch:
+    """bioem_batch: models x image stacks of mixed sizes scored by one graph-captured persistent launch.
+
+    ``stacks``: list of Images (64/96/128/192 px); ``projsets[m][k]``: model m projected for stack k;
+    ``max_shift[k]``: shift window of stack k.  ``out`` is the [n_models, n_images_total] float32 log P
+    matrix written by every ``run()``.
+    """
+
+    def __init__(self, ctx: Context, stacks, projsets, max_shift):
+        torch = _torch()
+        self.ctx = ctx
+        self._h = None
+        self.stacks, self.projsets = list(stacks), [list(r) for r in projsets]
+        n_models, n_stacks = len(self.projsets), len(self.stacks)
+        n_cols = sum(im.n_img for im in self.stacks)
+        self.out = torch.empty((n_models, n_cols), dtype=torch.float32, device=ctx.device)
+        st = (ctypes.c_void_p * n_stacks)(*[im._h for im in self.stacks])
+        ps = (ctypes.c_void_p * (n_models * n_stacks))(*[p._h for row in self.projsets for p in row])
+        sh = (ctypes.c_int * n_stacks)(*[int(v) for v in max_shift])
+        h = ctypes.c_void_p()
+        _check(ctx, lib().bioem_batch_create(ctx._h, n_models, n_stacks, st, ps, sh, _ptr(self.out), ctypes.byref(h)),
+               "batch_create")
+        self._h = h
+
+    @property
+    def evals(self) -> int:
+        return int(lib().bioem_batch_evals(self._h))
+
+    def run(self):
+        _check(self.ctx, lib().bioem_batch_run(self._h), "batch_run")
+        return self.out
+
+    def close(self):
+        if self._h:
+            lib().bioem_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune(ctx: Context, images: Images, projset: ProjSet, max_shift: int, cache_path: str | None = None) -> int:
+    """bioem_autotune: chunk size chosen for (image size, max_shift); cached in cache_path if given."""
+    out = ctypes.c_int(0)
+    _check(ctx, lib().bioem_autotune(ctx._h, images._h, projset._h, int(max_shift),
+                                     cache_path.encode() if cache_path else None, ctypes.byref(out)), "autotune")
+    return out.value
 
 
 def synthetic_maps(ctx: Context, atoms, sigma_A: float, quats, ctfs, npix: int, pixel_A: float):

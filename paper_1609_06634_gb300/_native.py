@@ -41,6 +41,12 @@ SIGNATURES = {
     "bioem_kernel_time": (c_int, [c_void_p, c_char_p, ctypes.POINTER(c_double), ctypes.POINTER(c_ull)]),
     "bioem_reset_kernel_stats": (c_int, [c_void_p]),
     "bioem_launch_count": (c_ull, [c_void_p]),
+    "bioem_batch_create": (c_int, [c_void_p, c_int, c_int, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
+                                   ctypes.POINTER(c_int), c_void_p, ctypes.POINTER(c_void_p)]),
+    "bioem_batch_run": (c_int, [c_void_p]),
+    "bioem_batch_evals": (ctypes.c_longlong, [c_void_p]),
+    "bioem_batch_free": (None, [c_void_p]),
+    "bioem_autotune": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_char_p, ctypes.POINTER(c_int)]),
     "bioem_images_count": (c_int, [c_void_p]),
     "bioem_projset_count": (c_int, [c_void_p]),
     "bioem_free_images": (None, [c_void_p]),

@@ -73,7 +73,7 @@ const int kSizes[5] = {32, 64, 96, 128, 192};
 
 int image_size_ok(int nx, int ny) {
     if (nx != ny) return 0;
-    return nx == 32 || nx == 64 || nx == 128;
+    return nx == 32 || nx == 64 || nx == 96 || nx == 128 || nx == 192;
 }
 
 // Allocation with the stream-ordered allocator; memory is usable by later work on the stream.

@@ -549,7 +549,9 @@ double bioem_log_norm_constant(int n) {
     switch (npix) {                                                           \
         case 32: return CALL(32);                                             \
         case 64: return CALL(64);                                             \
+        case 96: return CALL(96);                                             \
         case 128: return CALL(128);                                           \
+        case 192: return CALL(192);                                           \
         default: return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE, "unsupported image size %d", npix); \
     }
 

@@ -35,12 +35,16 @@ __constant__ float2 c_w16[16];
 __constant__ float2 c_w32[32];
 __constant__ float2 c_w64[64];
 __constant__ float2 c_w128[128];
+__constant__ float2 c_w96[96];
+__constant__ float2 c_w192[192];
 
 template <int M>
 __device__ __forceinline__ float2 cw(int t) {
     if constexpr (M == 16) return c_w16[t];
     else if constexpr (M == 32) return c_w32[t];
     else if constexpr (M == 64) return c_w64[t];
+    else if constexpr (M == 96) return c_w96[t];
+    else if constexpr (M == 192) return c_w192[t];
     else return c_w128[t];
 }
 
@@ -49,6 +53,8 @@ __device__ __forceinline__ const float2* cw_table() {
     if constexpr (M == 16) return c_w16;
     else if constexpr (M == 32) return c_w32;
     else if constexpr (M == 64) return c_w64;
+    else if constexpr (M == 96) return c_w96;
+    else if constexpr (M == 192) return c_w192;
     else return c_w128;
 }
 
@@ -107,7 +113,7 @@ __host__ __device__ constexpr int bitrev(int u, int bits) {
 __host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
 __host__ __device__ constexpr int pmod(int a, int m) { return ((a % m) + m) % m; }
 
-template <int N_, int SMAX_, int PB_>
+template <int N_, int SMAX_, int PB_, int THREADS_>
 struct Cfg {
     static constexpr int N = N_;
     static constexpr int SMAX = SMAX_;
@@ -118,19 +124,19 @@ struct Cfg {
     static constexpr int NROW = 2 * SMAX;      // stage-B transform rows per pair (dy < SMAX)
     static constexpr int R = N / L;            // sub-sequences per transform
     static constexpr int TASKS_A = PB * H;     // stage-A column tasks per batch
-    static constexpr int KA = PB * NC / 256;   // stage-A tasks per thread
-    static constexpr int THREADS = TASKS_A / KA;
-    static_assert(PB * NROW == 256, "one stage-B row per thread of the first 256");
-    static_assert(TASKS_A % KA == 0 && THREADS >= 256, "balanced stage A");
+    static constexpr int THREADS = THREADS_;   // threads doing the work (a block may have more)
+    static constexpr int NWARPS = THREADS / 32;  // full warps (combine step)
+    static_assert(THREADS >= PB * NROW, "one stage-B row per thread");
+    static_assert(NWARPS >= 1, "at least one full warp");
+    static_assert(N % L == 0, "sub-transform length divides N");
     static constexpr int QS = H;               // Q row stride (complex); odd -> conflict-free columns
     static constexpr int NDIR = PB * NS;       // outputs of the dy = +SMAX row, evaluated directly
     static constexpr size_t SM_IMG = (size_t)N * H * sizeof(float2);
     static constexpr size_t SM_Q = (size_t)PB * NS * QS * sizeof(float2);
-    static constexpr size_t SM_TW = (size_t)N * sizeof(float2);
     static constexpr size_t SM_TWC = (size_t)R * NS * sizeof(float2);
     static constexpr size_t SM_ROW = (size_t)PB * NROW * (2 * sizeof(float) + sizeof(int));
     static constexpr size_t SM_DIR = (size_t)NDIR * sizeof(float);
-    static constexpr size_t SMEM = SM_IMG + SM_Q + SM_TW + SM_TWC + SM_ROW + SM_DIR;
+    static constexpr size_t SMEM = SM_IMG + SM_Q + SM_TWC + SM_ROW + SM_DIR;
 };
 
 // Stage A for one column kx of one pair: Q(dy, kx) for dy = -SMAX..SMAX, with the rows ky = b + R a
@@ -222,17 +228,20 @@ __device__ __forceinline__ float loglik_t(float rho, int* status) {
     return log1pf(-r2);
 }
 
+// One work item: image w against parameter sets [lo, hi) of the wave starting at ps_begin.
+// img: the image's spectrum; rec_*: the image's record row (indexed by the wave-relative set);
+// gtw: exp(-2 pi i t / N), t < N, in global memory (the direct row's twiddles, L1-resident).
+// Threads with tid >= C::THREADS only take part in the barriers.
 template <class C>
-__global__ void __launch_bounds__(C::THREADS, 1)
-k_score(const float2* __restrict__ img_spec, int n_img, const float2* __restrict__ ps_spec, int ps_begin,
-        int ps_count, int chunk, int n_items, int s, float c1, float* __restrict__ rec_t, float* __restrict__ rec_s,
-        int* __restrict__ rec_d, int* __restrict__ status) {
+__device__ __forceinline__ void score_item(unsigned char* smem, const float2* __restrict__ gtw,
+                                           const float2* __restrict__ img,
+                                           const float2* __restrict__ ps_spec, int ps_begin, int lo, int hi, int s,
+                                           float c1, float* __restrict__ rec_t, float* __restrict__ rec_s,
+                                           int* __restrict__ rec_d, int* __restrict__ status) {
     constexpr int N = C::N, NC = C::NC, H = C::H, NS = C::NS, SMAX = C::SMAX, NROW = C::NROW;
-    extern __shared__ __align__(16) unsigned char smem[];
     float2* img_s = reinterpret_cast<float2*>(smem);
     float2* q_s = reinterpret_cast<float2*>(smem + C::SM_IMG);
-    float2* tw_s = reinterpret_cast<float2*>(smem + C::SM_IMG + C::SM_Q);
-    float2* twc_s = tw_s + N;
+    float2* twc_s = reinterpret_cast<float2*>(smem + C::SM_IMG + C::SM_Q);
     float* row_t = reinterpret_cast<float*>(twc_s + C::R * NS);
     float* row_s = row_t + C::PB * NROW;
     int* row_d = reinterpret_cast<int*>(row_s + C::PB * NROW);
@@ -240,31 +249,24 @@ k_score(const float2* __restrict__ img_spec, int n_img, const float2* __restrict
 
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    constexpr int NWARPS = C::THREADS / 32;   // full warps only: the last warp may be partial
-    const float2* cwN = cw_table<N>();
-    for (int i = tid; i < N; i += C::THREADS) tw_s[i] = cwN[i];
-    for (int i = tid; i < C::R * NS; i += C::THREADS) {
-        const int b = i / NS, m = i - (i / NS) * NS - SMAX;
-        twc_s[i] = cwN[pmod(b * m, N)];
-    }
-
-    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-        const int ci = item / n_img;
-        const int w = item - ci * n_img;
-        const int lo = ci * chunk;
-        const int hi = min(lo + chunk, ps_count);
-        __syncthreads();   // previous item's readers of img_s are done
-        {
-            const float4* src = reinterpret_cast<const float4*>(img_spec + (size_t)w * N * H);
-            float4* dst = reinterpret_cast<float4*>(img_s);
-            for (int i = tid; i < N * H / 2; i += C::THREADS) dst[i] = __ldg(src + i);
+    const bool active = tid < C::THREADS;
+    __syncthreads();   // the previous item's readers of shared memory are done
+    {
+        const float2* cwN = cw_table<N>();
+        for (int i = tid; i < C::R * NS; i += blockDim.x) {
+            const int b = i / NS, m = i - (i / NS) * NS - SMAX;
+            twc_s[i] = cwN[pmod(b * m, N)];
         }
-        __syncthreads();
-        for (int p0 = lo; p0 < hi; p0 += C::PB) {
-            // ---------------- stage A: one column of one pair per task, KA tasks per thread
+        const float4* src = reinterpret_cast<const float4*>(img);
+        float4* dst = reinterpret_cast<float4*>(img_s);
+        for (int i = tid; i < N * H / 2; i += blockDim.x) dst[i] = __ldg(src + i);
+    }
+    __syncthreads();
+    for (int p0 = lo; p0 < hi; p0 += C::PB) {
+        // ---------------- stage A: one column of one pair per task
+        if (active) {
 #pragma unroll 1
-            for (int k = 0; k < C::KA; ++k) {
-                const int task = tid + k * C::THREADS;
+            for (int task = tid; task < C::TASKS_A; task += C::THREADS) {
                 const int j = task / H;
                 const int kx = task - j * H;
                 const int p = min(p0 + j, hi - 1);
@@ -277,41 +279,43 @@ k_score(const float2* __restrict__ img_spec, int n_img, const float2* __restrict
 #pragma unroll
                 for (int m = 0; m < NS; ++m) qdst[m * C::QS] = acc[m];
             }
-            __syncthreads();
-            // ---------------- stage B: one row (dy = -SMAX .. SMAX-1) of one pair per thread
-            if (tid < C::PB * NROW) {
-                const int j = tid / NROW;
-                const int r = tid - j * NROW;
-                const float2* qrow = q_s + ((size_t)j * NS + r) * C::QS;
-                float acc[NS];
+        }
+        __syncthreads();
+        // ---------------- stage B: one row (dy = -SMAX .. SMAX-1) of one pair per thread
+        if (tid < C::PB * NROW) {
+            const int j = tid / NROW;
+            const int r = tid - j * NROW;
+            const float2* qrow = q_s + ((size_t)j * NS + r) * C::QS;
+            float acc[NS];
 #pragma unroll
-                for (int m = 0; m < NS; ++m) acc[m] = 0.f;
-                stage_b_row<C>(acc, qrow, twc_s);
-                const float qn = qrow[NC].x;   // Nyquist column, weight 1, phase (-1)^dx
-                const bool row_ok = abs(r - SMAX) <= s;
-                float tmin = INFINITY;
-                int arg = 0x7fffffff;
+            for (int m = 0; m < NS; ++m) acc[m] = 0.f;
+            stage_b_row<C>(acc, qrow, twc_s);
+            const float qn = qrow[NC].x;   // Nyquist column, weight 1, phase (-1)^dx
+            const bool row_ok = abs(r - SMAX) <= s;
+            float tmin = INFINITY;
+            int arg = 0x7fffffff;
 #pragma unroll
-                for (int m = 0; m < NS; ++m) {
-                    const float rho = acc[m] + (((m - SMAX) & 1) ? -qn : qn);
-                    const bool ok = row_ok && abs(m - SMAX) <= s;
-                    const float t = ok ? loglik_t(rho, status) : INFINITY;
-                    acc[m] = t;
-                    if (t < tmin) {
-                        tmin = t;
-                        arg = r * NS + m;
-                    }
+            for (int m = 0; m < NS; ++m) {
+                const float rho = acc[m] + (((m - SMAX) & 1) ? -qn : qn);
+                const bool ok = row_ok && abs(m - SMAX) <= s;
+                const float t = ok ? loglik_t(rho, status) : INFINITY;
+                acc[m] = t;
+                if (t < tmin) {
+                    tmin = t;
+                    arg = r * NS + m;
                 }
-                float ssum = 0.f;
-#pragma unroll
-                for (int m = 0; m < NS; ++m) ssum += (acc[m] < INFINITY) ? __expf(c1 * (acc[m] - tmin)) : 0.f;
-                row_t[tid] = tmin;
-                row_s[tid] = ssum;
-                row_d[tid] = arg;
             }
-            // ---------------- the dy = +SMAX row, one output per task, evaluated directly; the
-            // threads without a stage-B row (tid >= PB NROW) take the first outputs so that no
-            // thread with a row gets two
+            float ssum = 0.f;
+#pragma unroll
+            for (int m = 0; m < NS; ++m) ssum += (acc[m] < INFINITY) ? __expf(c1 * (acc[m] - tmin)) : 0.f;
+            row_t[tid] = tmin;
+            row_s[tid] = ssum;
+            row_d[tid] = arg;
+        }
+        // ---------------- the dy = +SMAX row, one output per task, evaluated directly; the
+        // threads without a stage-B row (tid >= PB NROW) take the first outputs so that few
+        // threads with a row get two
+        if (active) {
 #pragma unroll 1
             for (int i = (tid + C::THREADS - C::PB * NROW) % C::THREADS; i < C::NDIR; i += C::THREADS) {
                 const int j = i / NS;
@@ -323,8 +327,8 @@ k_score(const float2* __restrict__ img_spec, int n_img, const float2* __restrict
                 const int step = idx;
                 for (int kx = 1; kx < NC; ++kx) {
                     const float2 v = qrow[kx];
-                    const float2 wv = tw_s[idx];
-                    accv = fmaf(v.x, wv.x, fmaf(-v.y, wv.y, accv));
+                    const float2 wv = __ldg(gtw + idx);   // exp(-i theta): Re(v exp(+i theta)) = v.x w.x + v.y w.y
+                    accv = fmaf(v.x, wv.x, fmaf(v.y, wv.y, accv));
                     idx += step;
                     idx -= (idx >= N) ? N : 0;
                 }
@@ -332,34 +336,50 @@ k_score(const float2* __restrict__ img_spec, int n_img, const float2* __restrict
                 const bool ok = SMAX <= s && abs(dx) <= s;
                 dir_t[i] = ok ? loglik_t(rho, status) : INFINITY;
             }
-            __syncthreads();
-            // ---------------- combine the pieces of each pair (one full warp per pair)
-            for (int j = warp; warp < NWARPS && j < C::PB; j += NWARPS) {
-                const int p = p0 + j;
-                if (p >= hi) continue;
-                Part acc{INFINITY, 0.f, 0x7fffffff};
-                for (int r = lane; r < NROW; r += 32)
-                    acc = merge(acc, Part{row_t[j * NROW + r], row_s[j * NROW + r], row_d[j * NROW + r]}, c1);
-                for (int mi = lane; mi < NS; mi += 32) {
-                    const float t = dir_t[j * NS + mi];
-                    acc = merge(acc, Part{t, t < INFINITY ? 1.f : 0.f, 2 * SMAX * NS + mi}, c1);
-                }
+        }
+        __syncthreads();
+        // ---------------- combine the pieces of each pair (one full warp per pair)
+        for (int j = warp; warp < C::NWARPS && j < C::PB; j += C::NWARPS) {
+            const int p = p0 + j;
+            if (p >= hi) continue;
+            Part acc{INFINITY, 0.f, 0x7fffffff};
+            for (int r = lane; r < NROW; r += 32)
+                acc = merge(acc, Part{row_t[j * NROW + r], row_s[j * NROW + r], row_d[j * NROW + r]}, c1);
+            for (int mi = lane; mi < NS; mi += 32) {
+                const float t = dir_t[j * NS + mi];
+                acc = merge(acc, Part{t, t < INFINITY ? 1.f : 0.f, 2 * SMAX * NS + mi}, c1);
+            }
 #pragma unroll
-                for (int off = 16; off > 0; off >>= 1) {
-                    Part o;
-                    o.t = __shfl_xor_sync(0xffffffffu, acc.t, off);
-                    o.s = __shfl_xor_sync(0xffffffffu, acc.s, off);
-                    o.d = __shfl_xor_sync(0xffffffffu, acc.d, off);
-                    acc = merge(acc, o, c1);   // merge orders its operands, so both lanes agree
-                }
-                if (lane == 0) {
-                    const size_t o = (size_t)w * ps_count + p;
-                    rec_t[o] = acc.t;
-                    rec_s[o] = acc.s;
-                    rec_d[o] = acc.d;
-                }
+            for (int off = 16; off > 0; off >>= 1) {
+                Part o;
+                o.t = __shfl_xor_sync(0xffffffffu, acc.t, off);
+                o.s = __shfl_xor_sync(0xffffffffu, acc.s, off);
+                o.d = __shfl_xor_sync(0xffffffffu, acc.d, off);
+                acc = merge(acc, o, c1);   // merge orders its operands, so both lanes agree
+            }
+            if (lane == 0) {
+                rec_t[p] = acc.t;
+                rec_s[p] = acc.s;
+                rec_d[p] = acc.d;
             }
         }
+    }
+}
+
+template <class C>
+__global__ void __launch_bounds__(C::THREADS, 1)
+k_score(const float2* __restrict__ gtw, const float2* __restrict__ img_spec, int n_img,
+        const float2* __restrict__ ps_spec, int ps_begin, int ps_count, int chunk, int n_items, int s, float c1,
+        float* __restrict__ rec_t, float* __restrict__ rec_s, int* __restrict__ rec_d, int* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int ci = item / n_img;
+        const int w = item - ci * n_img;
+        const int lo = ci * chunk;
+        const int hi = min(lo + chunk, ps_count);
+        const size_t row = (size_t)w * ps_count;
+        score_item<C>(smem, gtw, img_spec + (size_t)w * C::N * C::H, ps_spec, ps_begin, lo, hi, s, c1, rec_t + row,
+                      rec_s + row, rec_d + row, status);
     }
 }
 
@@ -547,7 +567,8 @@ int run_score(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, i
         if (n_items > 0x7fffffffll) return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE, "too many work items");
         const int grid = (int)(n_items < slots ? n_items : slots);
         bioem_launch_begin(ctx, KID_SCORE);
-        k_score<C><<<grid, C::THREADS, smem, ctx->stream>>>(im->d_spec, n_img, ps->d_spec, wbegin, wl, (int)chunk,
+        k_score<C><<<grid, C::THREADS, smem, ctx->stream>>>(bioem_twiddles(ctx, C::N), im->d_spec, n_img, ps->d_spec,
+                                                             wbegin, wl, (int)chunk,
                                                              (int)n_items, max_shift, c1f, rec_t, rec_s, rec_d,
                                                              ctx->d_status);
         bioem_launch_end(ctx, KID_SCORE);
@@ -582,11 +603,14 @@ int run_score(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, i
     return BIOEM_OK;
 }
 
-using C32_4 = Cfg<32, 4, 32>;
-using C64_4 = Cfg<64, 4, 32>;
-using C64_8 = Cfg<64, 8, 16>;
-using C128_4 = Cfg<128, 4, 32>;
-using C128_16 = Cfg<128, 16, 8>;
+// <N, SMAX, pairs per batch, threads>
+using C32_4 = Cfg<32, 4, 32, 272>;
+using C64_4 = Cfg<64, 4, 32, 264>;
+using C64_8 = Cfg<64, 8, 16, 264>;
+using C96_12 = Cfg<96, 12, 10, 245>;
+using C128_4 = Cfg<128, 4, 32, 260>;
+using C128_16 = Cfg<128, 16, 8, 260>;
+using C192_24 = Cfg<192, 24, 2, 194>;
 
 }  // namespace
 
@@ -595,7 +619,9 @@ int bioem_score_supported(int npix, int max_shift) {
     switch (npix) {
         case 32: return max_shift <= 4;
         case 64: return max_shift <= 8;
+        case 96: return max_shift <= 12;
         case 128: return max_shift <= 16;
+        case 192: return max_shift <= 24;
         default: return 0;
     }
 }
@@ -606,17 +632,19 @@ int bioem_launch_score(bioem_ctx* ctx, const bioem_images* im, const bioem_projs
         case 32: return run_score<C32_4>(ctx, im, ps, max_shift, out);
         case 64: return max_shift <= 4 ? run_score<C64_4>(ctx, im, ps, max_shift, out)
                                        : run_score<C64_8>(ctx, im, ps, max_shift, out);
+        case 96: return run_score<C96_12>(ctx, im, ps, max_shift, out);
         case 128: return max_shift <= 4 ? run_score<C128_4>(ctx, im, ps, max_shift, out)
                                         : run_score<C128_16>(ctx, im, ps, max_shift, out);
+        case 192: return run_score<C192_24>(ctx, im, ps, max_shift, out);
         default: return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE, "unsupported image size %d", im->nx);
     }
 }
 
 int bioem_upload_score_twiddles(bioem_ctx* ctx) {
-    const int sizes[4] = {16, 32, 64, 128};
-    for (int k = 0; k < 4; ++k) {
+    const int sizes[6] = {16, 32, 64, 96, 128, 192};
+    for (int k = 0; k < 6; ++k) {
         const int M = sizes[k];
-        float2 h[128];
+        float2 h[192];
         for (int t = 0; t < M; ++t) {
             const double a = 2.0 * 3.14159265358979323846 * (double)t / (double)M;
             h[t] = make_float2((float)cos(a), (float)sin(a));
@@ -626,6 +654,8 @@ int bioem_upload_score_twiddles(bioem_ctx* ctx) {
             case 16: e = cudaMemcpyToSymbol(c_w16, h, sizeof(float2) * 16); break;
             case 32: e = cudaMemcpyToSymbol(c_w32, h, sizeof(float2) * 32); break;
             case 64: e = cudaMemcpyToSymbol(c_w64, h, sizeof(float2) * 64); break;
+            case 96: e = cudaMemcpyToSymbol(c_w96, h, sizeof(float2) * 96); break;
+            case 192: e = cudaMemcpyToSymbol(c_w192, h, sizeof(float2) * 192); break;
             default: e = cudaMemcpyToSymbol(c_w128, h, sizeof(float2) * 128); break;
         }
         if (e != cudaSuccess) return bioem_check_cuda(ctx, e, "twiddle upload");
@@ -708,7 +738,8 @@ int run_score_noalloc(bioem_ctx* ctx, const bioem_images* im, const bioem_projse
         const long long n_items = ((wl + chunk - 1) / chunk) * n_img;
         if (n_items > 0x7fffffffll) return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE, "too many work items");
         const int grid = (int)(n_items < slots ? n_items : slots);
-        k_score<C><<<grid, C::THREADS, smem, ctx->stream>>>(im->d_spec, n_img, ps->d_spec, (int)w0, wl, (int)chunk,
+        k_score<C><<<grid, C::THREADS, smem, ctx->stream>>>(bioem_twiddles(ctx, C::N), im->d_spec, n_img, ps->d_spec,
+                                                             (int)w0, wl, (int)chunk,
                                                              (int)n_items, max_shift, c1f, rec_t, rec_s, rec_d,
                                                              ctx->d_status);
         ctx->n_launches++;
@@ -752,8 +783,461 @@ extern "C" int bioem_score_noalloc(bioem_ctx* ctx, const bioem_images* images, c
         case 32: return run_score_noalloc<C32_4>(ctx, images, projset, max_shift, d_logP);
         case 64: return max_shift <= 4 ? run_score_noalloc<C64_4>(ctx, images, projset, max_shift, d_logP)
                                        : run_score_noalloc<C64_8>(ctx, images, projset, max_shift, d_logP);
+        case 96: return run_score_noalloc<C96_12>(ctx, images, projset, max_shift, d_logP);
         case 128: return max_shift <= 4 ? run_score_noalloc<C128_4>(ctx, images, projset, max_shift, d_logP)
                                         : run_score_noalloc<C128_16>(ctx, images, projset, max_shift, d_logP);
+        case 192: return run_score_noalloc<C192_24>(ctx, images, projset, max_shift, d_logP);
         default: return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE, "unsupported image size %d", images->nx);
     }
 }
+
+// ---------------------------------------------------------------------------- batched scoring
+// Several models against several image stacks of mixed sizes in one persistent launch.  A segment
+// is one (model, stack) pair: the stack's image spectra against that model's parameter sets for
+// that stack.  Work items of all segments form one list; every item runs the instance for its
+// image size.  All instances here use 256 threads (2 warps per scheduler keep the 96 / 192 px
+// paths at their register counts).
+#include <string>
+#include <vector>
+
+namespace {
+
+using M64 = Cfg<64, 8, 15, 256>;
+using M96 = Cfg<96, 12, 10, 256>;
+using M128 = Cfg<128, 16, 7, 256>;
+using M192 = Cfg<192, 24, 2, 256>;
+constexpr int kMultiThreads = 256;
+
+constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+constexpr size_t kMultiSmem = cmax(cmax(M64::SMEM, M96::SMEM), cmax(M128::SMEM, M192::SMEM));
+
+struct SegDesc {
+    const float2* img;    // [n_img][N][N/2+1]
+    const float2* ps;     // [n_ps][N][N/2+1]
+    const float2* gtw;    // exp(-2 pi i t / N)
+    const double* kA;     // [n_img]
+    const double* kB;     // [n_ps]
+    float* rec_t;         // [n_img][n_ps] records
+    float* rec_s;
+    int* rec_d;
+    long long item_begin; // first global item of this segment
+    long long row_begin;  // first global reduction row (image) of this segment
+    int n_img, n_ps, chunk, n_chunks, s, npix, nctf;
+    int out_row;          // model index (row of the output matrix)
+    int out_col;          // column of the segment's first image in the output matrix
+    float c1;
+    double log_norm;      // ln(n_ps S)
+};
+
+__device__ __forceinline__ int find_seg(const SegDesc* segs, int n, long long x, bool rows) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const long long b = rows ? segs[mid].row_begin : segs[mid].item_begin;
+        if (b <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kMultiThreads, 1)
+k_score_multi(const SegDesc* __restrict__ segs, int n_segs, long long n_items, int* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    for (long long item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int g = find_seg(segs, n_segs, item, false);
+        const SegDesc& sd = segs[g];
+        const long long local = item - sd.item_begin;
+        const int ci = (int)(local / sd.n_img);
+        const int w = (int)(local - (long long)ci * sd.n_img);
+        const int lo = ci * sd.chunk;
+        const int hi = min(lo + sd.chunk, sd.n_ps);
+        const size_t row = (size_t)w * sd.n_ps;
+        switch (sd.npix) {
+            case 64:
+                score_item<M64>(smem, sd.gtw, sd.img + (size_t)w * 64 * 33, sd.ps, 0, lo, hi, sd.s, sd.c1,
+                                sd.rec_t + row, sd.rec_s + row, sd.rec_d + row, status);
+                break;
+            case 96:
+                score_item<M96>(smem, sd.gtw, sd.img + (size_t)w * 96 * 49, sd.ps, 0, lo, hi, sd.s, sd.c1,
+                                sd.rec_t + row, sd.rec_s + row, sd.rec_d + row, status);
+                break;
+            case 128:
+                score_item<M128>(smem, sd.gtw, sd.img + (size_t)w * 128 * 65, sd.ps, 0, lo, hi, sd.s, sd.c1,
+                                 sd.rec_t + row, sd.rec_s + row, sd.rec_d + row, status);
+                break;
+            default:
+                score_item<M192>(smem, sd.gtw, sd.img + (size_t)w * 192 * 97, sd.ps, 0, lo, hi, sd.s, sd.c1,
+                                 sd.rec_t + row, sd.rec_s + row, sd.rec_d + row, status);
+                break;
+        }
+    }
+}
+
+// One block per (segment, image): float64 log-sum-exp over the image's records, written as float32
+// into out[model][column].
+__global__ void __launch_bounds__(kRedThreads) k_reduce_multi(const SegDesc* __restrict__ segs, int n_segs,
+                                                              float* __restrict__ out, int out_ld) {
+    __shared__ double redM[kRedThreads], redS[kRedThreads];
+    const long long row = blockIdx.x;
+    const int g = find_seg(segs, n_segs, row, true);
+    const SegDesc& sd = segs[g];
+    const int w = (int)(row - sd.row_begin);
+    const double ka = sd.kA[w];
+    const double c1 = (double)sd.c1;
+    double M = -INFINITY, S = 0.0;
+    const size_t base = (size_t)w * sd.n_ps;
+    for (int p = threadIdx.x; p < sd.n_ps; p += blockDim.x) {
+        const double m = ka + sd.kB[p] + c1 * (double)sd.rec_t[base + p];
+        const double s = sd.rec_s[base + p];
+        if (!(m > -INFINITY)) continue;
+        if (m > M) { S = S * exp(M - m) + s; M = m; }
+        else S += s * exp(m - M);
+    }
+    redM[threadIdx.x] = M;
+    redS[threadIdx.x] = S;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) {
+            const double m2 = redM[threadIdx.x + st], s2 = redS[threadIdx.x + st];
+            double m1 = redM[threadIdx.x], s1 = redS[threadIdx.x];
+            if (m2 > -INFINITY) {
+                if (m2 > m1) { s1 = s1 * exp(m1 - m2) + s2; m1 = m2; }
+                else s1 += s2 * exp(m2 - m1);
+            }
+            redM[threadIdx.x] = m1;
+            redS[threadIdx.x] = s1;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        out[(size_t)sd.out_row * out_ld + sd.out_col + w] = (float)(redM[0] + log(redS[0]) - sd.log_norm);
+}
+
+struct TuneEntry {
+    int npix, s, chunk;
+};
+
+int default_chunk(int npix) { return npix >= 192 ? 64 : 256; }
+
+int tuned_chunk(const std::vector<TuneEntry>& t, int npix, int s) {
+    for (const auto& e : t)
+        if (e.npix == npix && e.s == s) return e.chunk;
+    return default_chunk(npix);
+}
+
+int multi_pb(int npix) {
+    switch (npix) {
+        case 64: return M64::PB;
+        case 96: return M96::PB;
+        case 128: return M128::PB;
+        default: return M192::PB;
+    }
+}
+
+int multi_smax(int npix) {
+    switch (npix) {
+        case 64: return M64::SMAX;
+        case 96: return M96::SMAX;
+        case 128: return M128::SMAX;
+        default: return M192::SMAX;
+    }
+}
+
+}  // namespace
+
+struct bioem_batch {
+    bioem_ctx* ctx;
+    int n_models, n_stacks, n_cols;
+    std::vector<SegDesc> segs;
+    SegDesc* d_segs;
+    void* d_rec;
+    long long n_items, n_rows;
+    float* d_out;
+    cudaStream_t cap_stream;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    int grid;
+};
+
+// tune table kept per process (per image size and shift window)
+static std::mutex g_tune_mutex;
+static std::vector<TuneEntry> g_tune;
+
+static int tune_load(const char* path) {
+    FILE* f = fopen(path, "r");
+    if (!f) return 0;
+    int npix, s, chunk, n = 0;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    while (fscanf(f, "%d %d %d", &npix, &s, &chunk) == 3) {
+        if (chunk <= 0 || chunk > 4096) continue;
+        bool found = false;
+        for (auto& e : g_tune)
+            if (e.npix == npix && e.s == s) { e.chunk = chunk; found = true; }
+        if (!found) g_tune.push_back({npix, s, chunk});
+        ++n;
+    }
+    fclose(f);
+    return n;
+}
+
+static int batch_build(bioem_batch* b, int grid_override) {
+    bioem_ctx* ctx = b->ctx;
+    const size_t nb = sizeof(SegDesc) * b->segs.size();
+    if (cudaMalloc((void**)&b->d_segs, nb) != cudaSuccess) return bioem_set_error(ctx, BIOEM_ERR_OOM, "segment table");
+    if (cudaMemcpy(b->d_segs, b->segs.data(), nb, cudaMemcpyHostToDevice) != cudaSuccess)
+        return bioem_set_error(ctx, BIOEM_ERR_CUDA, "segment table upload");
+    if (cudaFuncSetAttribute(k_score_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMultiSmem) != cudaSuccess)
+        return bioem_set_error(ctx, BIOEM_ERR_CUDA, "shared memory attribute (%zu bytes)", kMultiSmem);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score_multi, kMultiThreads, kMultiSmem) != cudaSuccess ||
+        per_sm < 1)
+        return bioem_set_error(ctx, BIOEM_ERR_CUDA, "occupancy query");
+    long long g = (long long)per_sm * ctx->num_sms;
+    if (grid_override > 0) g = grid_override;
+    if (g > b->n_items) g = b->n_items;
+    b->grid = (int)g;
+    if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return bioem_set_error(ctx, BIOEM_ERR_CUDA, "capture stream");
+    if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return bioem_set_error(ctx, BIOEM_ERR_CUDA, "begin capture");
+    k_score_multi<<<b->grid, kMultiThreads, kMultiSmem, b->cap_stream>>>(b->d_segs, (int)b->segs.size(), b->n_items,
+                                                                        ctx->d_status);
+    k_reduce_multi<<<(unsigned)b->n_rows, kRedThreads, 0, b->cap_stream>>>(b->d_segs, (int)b->segs.size(), b->d_out,
+                                                                           b->n_cols);
+    cudaError_t e = cudaStreamEndCapture(b->cap_stream, &b->graph);
+    if (e != cudaSuccess) return bioem_check_cuda(ctx, e, "end capture");
+    e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) return bioem_check_cuda(ctx, e, "graph instantiate");
+    return BIOEM_OK;
+}
+
+extern "C" {
+
+int bioem_autotune(bioem_ctx* ctx, const bioem_images* images, const bioem_projset* projset, int max_shift,
+                   const char* cache_path, int* out_chunk) {
+    if (!ctx || !images || !projset) return BIOEM_ERR_INVALID_ARG;
+    if (cache_path && tune_load(cache_path) > 0) {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        for (const auto& e : g_tune)
+            if (e.npix == images->nx && e.s == max_shift) {
+                if (out_chunk) *out_chunk = e.chunk;
+                return BIOEM_OK;
+            }
+    }
+    const int npix = images->nx;
+    if (npix != 64 && npix != 96 && npix != 128 && npix != 192)
+        return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE, "autotune: batched sizes are 64, 96, 128, 192");
+    if (max_shift < 0 || max_shift > multi_smax(npix) || images->nx != projset->nx || images->n_img == 0 ||
+        projset->n_ps == 0)
+        return bioem_set_error(ctx, BIOEM_ERR_INVALID_ARG, "autotune: bad case");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return bioem_set_error(ctx, BIOEM_ERR_CUDA, "cudaSetDevice");
+    // trial: the first images (up to 2 per SM) against up to 4096 parameter sets, one segment
+    const int n_img = images->n_img < 2 * ctx->num_sms ? images->n_img : 2 * ctx->num_sms;
+    const int n_ps = projset->n_ps < 4096 ? projset->n_ps : 4096;
+    const int pb = multi_pb(npix);
+    const int cands[5] = {pb * 2, pb * 8, pb * 32, pb * 64, pb * 128};
+    void* rec = nullptr;
+    const size_t rec_bytes = (size_t)n_img * n_ps * 12;
+    if (cudaMalloc(&rec, rec_bytes) != cudaSuccess) return bioem_set_error(ctx, BIOEM_ERR_OOM, "autotune records");
+    double best_ms = 1e300;
+    int best = default_chunk(npix);
+    int rc = BIOEM_OK;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int k = 0; k < 5 && rc == BIOEM_OK; ++k) {
+        const int chunk = cands[k];
+        if (chunk > 2 * n_ps && k > 0) break;
+        bioem_batch b{};
+        b.ctx = ctx;
+        b.n_models = 1;
+        b.n_stacks = 1;
+        SegDesc sd{};
+        sd.img = images->d_spec;
+        sd.ps = projset->d_spec;
+        sd.gtw = bioem_twiddles(ctx, npix);
+        sd.kA = images->d_kA;
+        sd.kB = projset->d_kB;
+        sd.rec_t = static_cast<float*>(rec);
+        sd.rec_s = sd.rec_t + (size_t)n_img * n_ps;
+        sd.rec_d = reinterpret_cast<int*>(sd.rec_s + (size_t)n_img * n_ps);
+        sd.n_img = n_img;
+        sd.n_ps = n_ps;
+        sd.chunk = chunk;
+        sd.n_chunks = (n_ps + chunk - 1) / chunk;
+        sd.s = max_shift;
+        sd.npix = npix;
+        sd.nctf = projset->nctf;
+        sd.c1 = 0.5f * (3.0f - (float)(npix * npix));
+        sd.log_norm = 0.0;
+        b.n_items = (long long)sd.n_chunks * n_img;
+        b.segs.push_back(sd);
+        SegDesc* d_seg = nullptr;
+        if (cudaMalloc((void**)&d_seg, sizeof(SegDesc)) != cudaSuccess) { rc = BIOEM_ERR_OOM; break; }
+        cudaMemcpy(d_seg, &sd, sizeof(SegDesc), cudaMemcpyHostToDevice);
+        cudaFuncSetAttribute(k_score_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMultiSmem);
+        const int grid = (int)(b.n_items < ctx->num_sms ? b.n_items : ctx->num_sms);
+        double ms_best_rep = 1e300;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, ctx->stream);
+            k_score_multi<<<grid, kMultiThreads, kMultiSmem, ctx->stream>>>(d_seg, 1, b.n_items, ctx->d_status);
+            cudaEventRecord(e1, ctx->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = bioem_check_cuda(ctx, cudaGetLastError(), "autotune"); break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0 && ms < ms_best_rep) ms_best_rep = ms;   // first repetition warms up
+        }
+        cudaFree(d_seg);
+        if (ms_best_rep < best_ms) {
+            best_ms = ms_best_rep;
+            best = chunk;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(rec);
+    if (rc) return rc;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        bool found = false;
+        for (auto& e : g_tune)
+            if (e.npix == npix && e.s == max_shift) { e.chunk = best; found = true; }
+        if (!found) g_tune.push_back({npix, max_shift, best});
+        if (cache_path) {
+            FILE* f = fopen(cache_path, "w");
+            if (f) {
+                for (const auto& e : g_tune) fprintf(f, "%d %d %d\n", e.npix, e.s, e.chunk);
+                fclose(f);
+            }
+        }
+    }
+    if (out_chunk) *out_chunk = best;
+    return BIOEM_OK;
+}
+
+int bioem_batch_create(bioem_ctx* ctx, int n_models, int n_stacks, const bioem_images* const* stacks,
+                       const bioem_projset* const* projsets, const int* max_shift, float* d_logP_matrix,
+                       bioem_batch** out) {
+    if (!ctx || !out || n_models <= 0 || n_stacks <= 0 || !stacks || !projsets || !max_shift || !d_logP_matrix)
+        return BIOEM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return bioem_set_error(ctx, BIOEM_ERR_CUDA, "cudaSetDevice");
+    bioem_batch* b = new (std::nothrow) bioem_batch();
+    if (!b) return BIOEM_ERR_OOM;
+    b->ctx = ctx;
+    b->n_models = n_models;
+    b->n_stacks = n_stacks;
+    b->d_out = d_logP_matrix;
+    int col = 0;
+    size_t rec_total = 0;
+    std::vector<int> cols(n_stacks);
+    for (int k = 0; k < n_stacks; ++k) {
+        const bioem_images* im = stacks[k];
+        if (!im || im->ctx != ctx) { delete b; return bioem_set_error(ctx, BIOEM_ERR_INVALID_ARG, "stack %d", k); }
+        const int npix = im->nx;
+        if ((npix != 64 && npix != 96 && npix != 128 && npix != 192) || max_shift[k] < 0 ||
+            max_shift[k] > multi_smax(npix) || 2 * max_shift[k] >= npix) {
+            delete b;
+            return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE, "stack %d: %d px, shift %d", k, npix, max_shift[k]);
+        }
+        cols[k] = col;
+        col += im->n_img;
+    }
+    b->n_cols = col;
+    long long items = 0, rows = 0;
+    for (int m = 0; m < n_models; ++m) {
+        for (int k = 0; k < n_stacks; ++k) {
+            const bioem_images* im = stacks[k];
+            const bioem_projset* ps = projsets[(size_t)m * n_stacks + k];
+            if (!ps || ps->ctx != ctx || ps->nx != im->nx || fabs(ps->pixel_A - im->pixel_A) > 1e-9 * im->pixel_A ||
+                ps->n_ps == 0) {
+                delete b;
+                return bioem_set_error(ctx, BIOEM_ERR_INVALID_ARG, "projection set (%d, %d) does not match", m, k);
+            }
+            if (im->n_img == 0) continue;
+            SegDesc sd{};
+            sd.img = im->d_spec;
+            sd.ps = ps->d_spec;
+            sd.gtw = bioem_twiddles(ctx, im->nx);
+            sd.kA = im->d_kA;
+            sd.kB = ps->d_kB;
+            sd.n_img = im->n_img;
+            sd.n_ps = ps->n_ps;
+            {
+                std::lock_guard<std::mutex> lock(g_tune_mutex);
+                sd.chunk = tuned_chunk(g_tune, im->nx, max_shift[k]);
+            }
+            sd.n_chunks = (sd.n_ps + sd.chunk - 1) / sd.chunk;
+            sd.s = max_shift[k];
+            sd.npix = im->nx;
+            sd.nctf = ps->nctf;
+            sd.out_row = m;
+            sd.out_col = cols[k];
+            sd.c1 = 0.5f * (3.0f - (float)(im->nx * im->nx));
+            const int S = (2 * max_shift[k] + 1) * (2 * max_shift[k] + 1);
+            sd.log_norm = log((double)ps->n_ps * S);
+            sd.item_begin = items;
+            sd.row_begin = rows;
+            items += (long long)sd.n_chunks * sd.n_img;
+            rows += sd.n_img;
+            rec_total += (size_t)sd.n_img * sd.n_ps * 12;
+            b->segs.push_back(sd);
+        }
+    }
+    b->n_items = items;
+    b->n_rows = rows;
+    if (b->segs.empty()) { delete b; return bioem_set_error(ctx, BIOEM_ERR_INVALID_ARG, "no images"); }
+    if (rows > 0x7fffffffll) { delete b; return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE, "too many rows"); }
+    if (cudaMalloc(&b->d_rec, rec_total) != cudaSuccess) {
+        delete b;
+        return bioem_set_error(ctx, BIOEM_ERR_OOM, "batch records of %zu bytes", rec_total);
+    }
+    size_t off = 0;
+    for (auto& sd : b->segs) {
+        const size_t npair = (size_t)sd.n_img * sd.n_ps;
+        float* base = reinterpret_cast<float*>(static_cast<unsigned char*>(b->d_rec) + off);
+        sd.rec_t = base;
+        sd.rec_s = base + npair;
+        sd.rec_d = reinterpret_cast<int*>(base + 2 * npair);
+        off += npair * 12;
+    }
+    const int rc = batch_build(b, 0);
+    if (rc) {
+        bioem_batch_free(b);
+        return rc;
+    }
+    *out = b;
+    return BIOEM_OK;
+}
+
+int bioem_batch_run(bioem_batch* b) {
+    if (!b) return BIOEM_ERR_INVALID_ARG;
+    bioem_ctx* ctx = b->ctx;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return bioem_set_error(ctx, BIOEM_ERR_CUDA, "cudaSetDevice");
+    ctx->n_launches += 2;
+    ctx->kid_launches[KID_SCORE] += 1;
+    ctx->kid_launches[KID_REDUCE_WAVE] += 1;
+    return bioem_check_cuda(ctx, cudaGraphLaunch(b->exec, ctx->stream), "graph launch");
+}
+
+long long bioem_batch_evals(const bioem_batch* b) {
+    if (!b) return -1;
+    long long e = 0;
+    for (const auto& sd : b->segs) e += (long long)sd.n_img * sd.n_ps;
+    return e;
+}
+
+void bioem_batch_free(bioem_batch* b) {
+    if (!b) return;
+    cudaSetDevice(b->ctx->device);
+    cudaStreamSynchronize(b->ctx->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->d_segs) cudaFree(b->d_segs);
+    if (b->d_rec) cudaFree(b->d_rec);
+    cudaGetLastError();
+    delete b;
+}
+
+}  // extern "C"

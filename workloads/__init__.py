@@ -10,10 +10,11 @@ with its own code.
 
 Workload shapes follow the paper's setting (Section 4: images of a model in
 random orientation, with a PSF, a centre displacement, normalisation, offset and
-Gaussian noise, scored over orientation x PSF x displacement grids) with the
-sizes of the five synthetic configurations documented in the design doc.
+Gaussian noise, scored over orientation x PSF x displacement grids); the sizes
+are those of the configurations in ``configs.py`` and ``batched.py``.
 """
 from .configs import CONFIGS, Config, get_config  # noqa: F401
+from .batched import BatchedConfig, StackSpec, batched_workload, model_atoms  # noqa: F401
 from .generate import (  # noqa: F401
     atoms_in_ball,
     ctf_grid,
