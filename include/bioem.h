@@ -40,6 +40,7 @@ typedef struct bioem_ctx bioem_ctx;
 typedef struct bioem_images bioem_images;
 typedef struct bioem_projset bioem_projset;
 typedef struct bioem_batch bioem_batch;
+typedef struct bioem_cnn bioem_cnn;
 
 /* One point of the PSF grid, in physical units (the CTF and envelope after Eq. 4).
  * Converted to the paper's coefficients as a = lambda_e * defocus_A / (2 pi),
@@ -190,6 +191,49 @@ void bioem_batch_free(bioem_batch* batch);
  * "npix shift chunk" lines.  *out_chunk (may be NULL) receives the choice. */
 int bioem_autotune(bioem_ctx* ctx, const bioem_images* images, const bioem_projset* projset, int max_shift,
                    const char* cache_path, int* out_chunk);
+
+/* Scoring of per-image lists of parameter sets (the paper has no counterpart: it scores every
+ * image on the full grid; this serves proposals that restrict each image to a few grid cells).
+ * Image w is scored against projset sets d_ps_idx[d_offsets[w] .. d_offsets[w+1]) (CSR, device
+ * int arrays; at most max_per_image per image), every displacement |d| <= max_shift, and the
+ * results are folded into d_acc [n_img][2] float64 device = running (max, sum exp(. - max)) of
+ * ln L over everything scored so far; first != 0 overwrites d_acc instead of folding into it.
+ * bioem_acc_logP turns the accumulators into ln P: d_logP[w] = max + ln sum - log_norm (pass
+ * log_norm = ln(number of sets scored per image x S)).  Calling it over several projection sets
+ * (waves of grid cells) accumulates one posterior. */
+int bioem_score_gathered(bioem_ctx* ctx, const bioem_images* images, const bioem_projset* projset, int max_shift,
+                         const int* d_offsets, const int* d_ps_idx, int nnz, int max_per_image, double* d_acc,
+                         int first);
+int bioem_acc_logP(bioem_ctx* ctx, const double* d_acc, int n_img, double log_norm, double* d_logP);
+
+/* Learned orientation / defocus proposal (no counterpart in the paper).  A convolutional network
+ * on the image averaged over downsample x downsample pixels and standardised: six 3x3 convolutions
+ * of `channels` channels (strides 1, 2, 1, 2, 1, 2; ReLU), then two linear heads: n_qbins coarse
+ * orientation bins and n_dbins defocus bins.  Trained by the library's own forward / backward
+ * kernels (cross-entropy of both heads, Adam on float32 master weights, float16 weights in the
+ * passes).  image_px / downsample must be a multiple of 8; batches hold at most max_batch images
+ * [B][image_px][image_px] float32 (device).  Flat parameter order: per conv layer W[co][ci][3][3],
+ * b[co]; then Wq[n_qbins][F], bq, Wd[n_dbins][F], bd, F = channels (image_px/downsample/8)^2.
+ *   bioem_cnn_create      counter-based uniform initialisation from `seed` (biases zero)
+ *   bioem_cnn_gradients   loss per sample [B] and all gradients (mean over the batch) [n_params]
+ *   bioem_cnn_train_step  gradients then one Adam step with learning rate lr
+ *   bioem_cnn_forward     logits [B][n_qbins], [B][n_dbins] (either may be NULL)
+ *   bioem_propose         for n images (any count; processed in batches), the k joint bins
+ *                         q * n_dbins + d with the largest log_softmax(q) + log_softmax(d), best
+ *                         first, ties to the lower bin: d_bins [n][k] int, d_scores [n][k] (may be NULL)
+ * Errors: INVALID_ARG, OOM, CUDA. */
+int bioem_cnn_create(bioem_ctx* ctx, int image_px, int downsample, int channels, int n_qbins, int n_dbins,
+                     int max_batch, unsigned long long seed, bioem_cnn** out);
+long long bioem_cnn_num_params(const bioem_cnn* cnn);
+int bioem_cnn_set_params(bioem_cnn* cnn, const float* d_params);
+int bioem_cnn_get_params(bioem_cnn* cnn, float* d_params);
+int bioem_cnn_forward(bioem_cnn* cnn, const float* d_images, int B, float* d_logits_q, float* d_logits_d);
+int bioem_cnn_gradients(bioem_cnn* cnn, const float* d_images, const int* d_label_q, const int* d_label_d, int B,
+                        float* d_grads, float* d_loss);
+int bioem_cnn_train_step(bioem_cnn* cnn, const float* d_images, const int* d_label_q, const int* d_label_d, int B,
+                         float lr, float* d_loss);
+int bioem_propose(bioem_cnn* cnn, const float* d_images, int n, int k, int* d_bins, float* d_scores);
+void bioem_cnn_free(bioem_cnn* cnn);
 
 /* Measurement hooks.  bioem_launch_count: kernels the library has launched with this context
  * since creation or the last reset.  With timing enabled, CUDA events are recorded on the

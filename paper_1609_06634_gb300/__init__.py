@@ -15,7 +15,7 @@ from . import _native
 from ._native import CTF
 
 __all__ = ["BioEMError", "Context", "Images", "ProjSet", "prepare_images", "project_model", "score", "score_all",
-           "best_params", "score_pairs", "score_noalloc", "Batch", "autotune", "synthetic_maps", "ctf_array", "lib"]
+           "best_params", "score_pairs", "score_noalloc", "Batch", "autotune", "CNN", "score_gathered", "acc_logP", "synthetic_maps", "ctf_array", "lib"]
 
 OK = 0
 ERR_INVALID_ARG, ERR_UNSUPPORTED_SIZE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NUMERIC = -1, -2, -3, -4, -5, -6
@@ -290,6 +290,110 @@ def autotune(ctx: Context, images: Images, projset: ProjSet, max_shift: int, cac
     _check(ctx, lib().bioem_autotune(ctx._h, images._h, projset._h, int(max_shift),
                                      cache_path.encode() if cache_path else None, ctypes.byref(out)), "autotune")
     return out.value
+
+
+class CNN:
+    """bioem_cnn: the learned orientation / defocus proposal network (own CUDA kernels)."""
+
+    def __init__(self, ctx: Context, image_px: int = 128, downsample: int = 2, channels: int = 32,
+                 n_qbins: int = 4608, n_dbins: int = 4, max_batch: int = 256, seed: int = 0):
+        self.ctx = ctx
+        self._h = None
+        h = ctypes.c_void_p()
+        _check(ctx, lib().bioem_cnn_create(ctx._h, image_px, downsample, channels, n_qbins, n_dbins, max_batch,
+                                           int(seed), ctypes.byref(h)), "cnn_create")
+        self._h = h
+        self.image_px, self.n_qbins, self.n_dbins, self.max_batch = image_px, n_qbins, n_dbins, max_batch
+        self.n_params = int(lib().bioem_cnn_num_params(h))
+
+    def _imgs(self, images):
+        torch = _torch()
+        t = _dev_tensor(images, torch.float32, self.ctx.device, "images", ndim=3)
+        if t.shape[1] != self.image_px or t.shape[2] != self.image_px:
+            raise BioEMError(ERR_INVALID_ARG, "image size does not match the network")
+        return t
+
+    def _labels(self, y):
+        torch = _torch()
+        return _dev_tensor(y, torch.int32, self.ctx.device, "labels", ndim=1)
+
+    def set_params(self, theta):
+        torch = _torch()
+        t = _dev_tensor(theta, torch.float32, self.ctx.device, "params", ndim=1)
+        _check(self.ctx, lib().bioem_cnn_set_params(self._h, _ptr(t)), "cnn_set_params")
+
+    def get_params(self):
+        torch = _torch()
+        out = torch.empty(self.n_params, dtype=torch.float32, device=self.ctx.device)
+        _check(self.ctx, lib().bioem_cnn_get_params(self._h, _ptr(out)), "cnn_get_params")
+        return out
+
+    def forward(self, images):
+        torch = _torch()
+        t = self._imgs(images)
+        lq = torch.empty((t.shape[0], self.n_qbins), dtype=torch.float32, device=self.ctx.device)
+        ld = torch.empty((t.shape[0], self.n_dbins), dtype=torch.float32, device=self.ctx.device)
+        _check(self.ctx, lib().bioem_cnn_forward(self._h, _ptr(t), t.shape[0], _ptr(lq), _ptr(ld)), "cnn_forward")
+        return lq, ld
+
+    def gradients(self, images, yq, yd):
+        torch = _torch()
+        t = self._imgs(images)
+        g = torch.empty(self.n_params, dtype=torch.float32, device=self.ctx.device)
+        loss = torch.empty(t.shape[0], dtype=torch.float32, device=self.ctx.device)
+        _check(self.ctx, lib().bioem_cnn_gradients(self._h, _ptr(t), _ptr(self._labels(yq)), _ptr(self._labels(yd)),
+                                                   t.shape[0], _ptr(g), _ptr(loss)), "cnn_gradients")
+        return g, loss
+
+    def train_step(self, images, yq, yd, lr: float, loss_out=None):
+        torch = _torch()
+        t = self._imgs(images)
+        if loss_out is None:
+            loss_out = torch.empty(t.shape[0], dtype=torch.float32, device=self.ctx.device)
+        _check(self.ctx, lib().bioem_cnn_train_step(self._h, _ptr(t), _ptr(self._labels(yq)), _ptr(self._labels(yd)),
+                                                    t.shape[0], float(lr), _ptr(loss_out)), "cnn_train_step")
+        return loss_out
+
+    def propose(self, images, k: int):
+        torch = _torch()
+        t = self._imgs(images)
+        bins = torch.empty((t.shape[0], k), dtype=torch.int32, device=self.ctx.device)
+        scores = torch.empty((t.shape[0], k), dtype=torch.float32, device=self.ctx.device)
+        _check(self.ctx, lib().bioem_propose(self._h, _ptr(t), t.shape[0], int(k), _ptr(bins), _ptr(scores)), "propose")
+        return bins, scores
+
+    def close(self):
+        if self._h:
+            lib().bioem_cnn_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def score_gathered(ctx: Context, images: Images, projset: ProjSet, max_shift: int, offsets, ps_idx,
+                   max_per_image: int, acc, first: bool):
+    """bioem_score_gathered: fold image w's scores over projset sets ps_idx[offsets[w]:offsets[w+1]] into acc."""
+    torch = _torch()
+    o = _dev_tensor(offsets, torch.int32, ctx.device, "offsets", ndim=1)
+    p = _dev_tensor(ps_idx, torch.int32, ctx.device, "ps_idx", ndim=1)
+    a = _dev_tensor(acc, torch.float64, ctx.device, "acc", ndim=2, last=2)
+    if a.data_ptr() != acc.data_ptr():
+        raise BioEMError(ERR_INVALID_ARG, "acc must be contiguous")
+    _check(ctx, lib().bioem_score_gathered(ctx._h, images._h, projset._h, int(max_shift), _ptr(o), _ptr(p), p.shape[0],
+                                           int(max_per_image), _ptr(a), 1 if first else 0), "score_gathered")
+    return acc
+
+
+def acc_logP(ctx: Context, acc, log_norm: float):
+    torch = _torch()
+    a = _dev_tensor(acc, torch.float64, ctx.device, "acc", ndim=2, last=2)
+    out = torch.empty(a.shape[0], dtype=torch.float64, device=ctx.device)
+    _check(ctx, lib().bioem_acc_logP(ctx._h, _ptr(a), a.shape[0], float(log_norm), _ptr(out)), "acc_logP")
+    return out
 
 
 def synthetic_maps(ctx: Context, atoms, sigma_A: float, quats, ctfs, npix: int, pixel_A: float):

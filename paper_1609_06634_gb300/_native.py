@@ -47,6 +47,18 @@ SIGNATURES = {
     "bioem_batch_evals": (ctypes.c_longlong, [c_void_p]),
     "bioem_batch_free": (None, [c_void_p]),
     "bioem_autotune": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_char_p, ctypes.POINTER(c_int)]),
+    "bioem_score_gathered": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_int, c_int, c_void_p,
+                                     c_int]),
+    "bioem_acc_logP": (c_int, [c_void_p, c_void_p, c_int, c_double, c_void_p]),
+    "bioem_cnn_create": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_int, c_ull, ctypes.POINTER(c_void_p)]),
+    "bioem_cnn_num_params": (ctypes.c_longlong, [c_void_p]),
+    "bioem_cnn_set_params": (c_int, [c_void_p, c_void_p]),
+    "bioem_cnn_get_params": (c_int, [c_void_p, c_void_p]),
+    "bioem_cnn_forward": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p]),
+    "bioem_cnn_gradients": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p]),
+    "bioem_cnn_train_step": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, ctypes.c_float, c_void_p]),
+    "bioem_propose": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p]),
+    "bioem_cnn_free": (None, [c_void_p]),
     "bioem_images_count": (c_int, [c_void_p]),
     "bioem_projset_count": (c_int, [c_void_p]),
     "bioem_free_images": (None, [c_void_p]),

@@ -234,7 +234,7 @@ __device__ __forceinline__ float loglik_t(float rho, int* status) {
 // Threads with tid >= C::THREADS only take part in the barriers.
 template <class C>
 __device__ __forceinline__ void score_item(unsigned char* smem, const float2* __restrict__ gtw,
-                                           const float2* __restrict__ img,
+                                           const float2* __restrict__ img, const int* __restrict__ ps_idx,
                                            const float2* __restrict__ ps_spec, int ps_begin, int lo, int hi, int s,
                                            float c1, float* __restrict__ rec_t, float* __restrict__ rec_s,
                                            int* __restrict__ rec_d, int* __restrict__ status) {
@@ -270,7 +270,8 @@ __device__ __forceinline__ void score_item(unsigned char* smem, const float2* __
                 const int j = task / H;
                 const int kx = task - j * H;
                 const int p = min(p0 + j, hi - 1);
-                const float2* ps_col = ps_spec + (size_t)(ps_begin + p) * N * H + kx;
+                const int gp = ps_idx ? __ldg(ps_idx + p) : ps_begin + p;
+                const float2* ps_col = ps_spec + (size_t)gp * N * H + kx;
                 float2 acc[NS];
 #pragma unroll
                 for (int m = 0; m < NS; ++m) acc[m] = make_float2(0.f, 0.f);
@@ -378,7 +379,7 @@ k_score(const float2* __restrict__ gtw, const float2* __restrict__ img_spec, int
         const int lo = ci * chunk;
         const int hi = min(lo + chunk, ps_count);
         const size_t row = (size_t)w * ps_count;
-        score_item<C>(smem, gtw, img_spec + (size_t)w * C::N * C::H, ps_spec, ps_begin, lo, hi, s, c1, rec_t + row,
+        score_item<C>(smem, gtw, img_spec + (size_t)w * C::N * C::H, nullptr, ps_spec, ps_begin, lo, hi, s, c1, rec_t + row,
                       rec_s + row, rec_d + row, status);
     }
 }
@@ -854,19 +855,19 @@ k_score_multi(const SegDesc* __restrict__ segs, int n_segs, long long n_items, i
         const size_t row = (size_t)w * sd.n_ps;
         switch (sd.npix) {
             case 64:
-                score_item<M64>(smem, sd.gtw, sd.img + (size_t)w * 64 * 33, sd.ps, 0, lo, hi, sd.s, sd.c1,
+                score_item<M64>(smem, sd.gtw, sd.img + (size_t)w * 64 * 33, nullptr, sd.ps, 0, lo, hi, sd.s, sd.c1,
                                 sd.rec_t + row, sd.rec_s + row, sd.rec_d + row, status);
                 break;
             case 96:
-                score_item<M96>(smem, sd.gtw, sd.img + (size_t)w * 96 * 49, sd.ps, 0, lo, hi, sd.s, sd.c1,
+                score_item<M96>(smem, sd.gtw, sd.img + (size_t)w * 96 * 49, nullptr, sd.ps, 0, lo, hi, sd.s, sd.c1,
                                 sd.rec_t + row, sd.rec_s + row, sd.rec_d + row, status);
                 break;
             case 128:
-                score_item<M128>(smem, sd.gtw, sd.img + (size_t)w * 128 * 65, sd.ps, 0, lo, hi, sd.s, sd.c1,
+                score_item<M128>(smem, sd.gtw, sd.img + (size_t)w * 128 * 65, nullptr, sd.ps, 0, lo, hi, sd.s, sd.c1,
                                  sd.rec_t + row, sd.rec_s + row, sd.rec_d + row, status);
                 break;
             default:
-                score_item<M192>(smem, sd.gtw, sd.img + (size_t)w * 192 * 97, sd.ps, 0, lo, hi, sd.s, sd.c1,
+                score_item<M192>(smem, sd.gtw, sd.img + (size_t)w * 192 * 97, nullptr, sd.ps, 0, lo, hi, sd.s, sd.c1,
                                  sd.rec_t + row, sd.rec_s + row, sd.rec_d + row, status);
                 break;
         }
@@ -1238,6 +1239,167 @@ void bioem_batch_free(bioem_batch* b) {
     if (b->d_rec) cudaFree(b->d_rec);
     cudaGetLastError();
     delete b;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------- gathered scoring
+// Each image against its own list of parameter sets (CSR: offsets[n_img + 1], ps_idx[nnz] into the
+// projection set), folded into running per-image float64 (max, sum) accumulators.
+namespace {
+
+template <class C>
+__global__ void __launch_bounds__(C::THREADS, 1)
+k_score_gathered(const float2* __restrict__ gtw, const float2* __restrict__ img_spec, int n_img,
+                 const int* __restrict__ offsets, const int* __restrict__ ps_idx, const float2* __restrict__ ps_spec,
+                 int chunk, int chunks_per_img, int s, float c1, float* __restrict__ rec_t, float* __restrict__ rec_s,
+                 int* __restrict__ rec_d, int* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const long long n_items = (long long)n_img * chunks_per_img;
+    for (long long item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int ci = (int)(item / n_img);
+        const int w = (int)(item - (long long)ci * n_img);
+        const int b0 = offsets[w], b1 = offsets[w + 1];
+        const int lo = ci * chunk;
+        const int hi = min(lo + chunk, b1 - b0);
+        if (lo >= hi) continue;   // uniform across the block: no barrier is skipped by a subset
+        score_item<C>(smem, gtw, img_spec + (size_t)w * C::N * C::H, ps_idx + b0, ps_spec, 0, lo, hi, s, c1,
+                      rec_t + b0, rec_s + b0, rec_d + b0, status);
+    }
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_fold_gathered(const int* __restrict__ offsets,
+                                                               const int* __restrict__ ps_idx,
+                                                               const float* __restrict__ rec_t,
+                                                               const float* __restrict__ rec_s,
+                                                               const double* __restrict__ kA,
+                                                               const double* __restrict__ kB, double c1,
+                                                               double* __restrict__ acc, int first) {
+    __shared__ double redM[kRedThreads], redS[kRedThreads];
+    const int w = blockIdx.x;
+    const int b0 = offsets[w], b1 = offsets[w + 1];
+    double M = -INFINITY, S = 0.0;
+    for (int i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+        const double m = kA[w] + kB[ps_idx[i]] + c1 * (double)rec_t[i];
+        const double sv = rec_s[i];
+        if (!(m > -INFINITY)) continue;
+        if (m > M) { S = S * exp(M - m) + sv; M = m; }
+        else S += sv * exp(m - M);
+    }
+    redM[threadIdx.x] = M;
+    redS[threadIdx.x] = S;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) {
+            const double m2 = redM[threadIdx.x + st], s2 = redS[threadIdx.x + st];
+            double m1 = redM[threadIdx.x], s1 = redS[threadIdx.x];
+            if (m2 > -INFINITY) {
+                if (m2 > m1) { s1 = s1 * exp(m1 - m2) + s2; m1 = m2; }
+                else s1 += s2 * exp(m2 - m1);
+            }
+            redM[threadIdx.x] = m1;
+            redS[threadIdx.x] = s1;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double m1 = redM[0], s1 = redS[0];
+        if (!first) {
+            const double m2 = acc[2 * w], s2 = acc[2 * w + 1];
+            if (m2 > -INFINITY) {
+                if (m2 > m1) { s1 = s1 * exp(m1 - m2) + s2; m1 = m2; }
+                else s1 += s2 * exp(m2 - m1);
+            }
+        }
+        acc[2 * w] = m1;
+        acc[2 * w + 1] = s1;
+    }
+}
+
+__global__ void k_acc_logP(const double* __restrict__ acc, int n_img, double log_norm, double* __restrict__ logP) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w < n_img) logP[w] = acc[2 * w] + log(acc[2 * w + 1]) - log_norm;
+}
+
+template <class C>
+int run_gathered(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, int max_shift, const int* offsets,
+                 const int* ps_idx, int nnz, int max_per_image, double* acc, int first) {
+    const int n_img = im->n_img;
+    const size_t need = (size_t)nnz * 12;
+    if (ctx->rec_bytes < need) {
+        if (ctx->d_rec) cudaFreeAsync(ctx->d_rec, ctx->stream);
+        ctx->d_rec = nullptr;
+        ctx->rec_bytes = 0;
+        if (cudaMallocAsync(&ctx->d_rec, need, ctx->stream) != cudaSuccess)
+            return bioem_set_error(ctx, BIOEM_ERR_OOM, "record scratch of %zu bytes", need);
+        ctx->rec_bytes = need;
+    }
+    float* rec_t = reinterpret_cast<float*>(ctx->d_rec);
+    float* rec_s = rec_t + nnz;
+    int* rec_d = reinterpret_cast<int*>(rec_s + nnz);
+    const size_t smem = C::SMEM;
+    if (cudaFuncSetAttribute(k_score_gathered<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return bioem_set_error(ctx, BIOEM_ERR_CUDA, "shared memory attribute");
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score_gathered<C>, C::THREADS, smem);
+    if (per_sm < 1) per_sm = 1;
+    int chunk = 256;
+    const int cpi = (max_per_image + chunk - 1) / chunk;
+    const long long items = (long long)n_img * cpi;
+    const int grid = (int)(items < (long long)per_sm * ctx->num_sms ? items : (long long)per_sm * ctx->num_sms);
+    const int n = C::N * C::N;
+    if (grid > 0) {
+        bioem_launch_begin(ctx, KID_SCORE);
+        k_score_gathered<C><<<grid, C::THREADS, smem, ctx->stream>>>(bioem_twiddles(ctx, C::N), im->d_spec, n_img, offsets,
+                                                                     ps_idx, ps->d_spec, chunk, cpi, max_shift,
+                                                                     0.5f * (3.0f - (float)n), rec_t, rec_s, rec_d,
+                                                                     ctx->d_status);
+        bioem_launch_end(ctx, KID_SCORE);
+        int rc = bioem_check_cuda(ctx, cudaGetLastError(), "k_score_gathered");
+        if (rc) return rc;
+    }
+    bioem_launch_begin(ctx, KID_REDUCE_WAVE);
+    k_fold_gathered<<<n_img, kRedThreads, 0, ctx->stream>>>(offsets, ps_idx, rec_t, rec_s, im->d_kA, ps->d_kB,
+                                                           0.5 * (3.0 - (double)n), acc, first);
+    bioem_launch_end(ctx, KID_REDUCE_WAVE);
+    return bioem_check_cuda(ctx, cudaGetLastError(), "k_fold_gathered");
+}
+
+}  // namespace
+
+extern "C" {
+
+int bioem_score_gathered(bioem_ctx* ctx, const bioem_images* images, const bioem_projset* projset, int max_shift,
+                         const int* d_offsets, const int* d_ps_idx, int nnz, int max_per_image, double* d_acc,
+                         int first) {
+    if (!ctx || !images || !projset || !d_offsets || !d_acc || nnz < 0 || max_per_image < 0 || (nnz > 0 && !d_ps_idx))
+        return BIOEM_ERR_INVALID_ARG;
+    if (images->ctx != ctx || projset->ctx != ctx || images->nx != projset->nx)
+        return bioem_set_error(ctx, BIOEM_ERR_INVALID_ARG, "images and projections do not match");
+    if (!bioem_score_supported(images->nx, max_shift))
+        return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE, "max_shift %d unsupported at %d px", max_shift,
+                               images->nx);
+    if (images->n_img == 0) return BIOEM_OK;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return bioem_set_error(ctx, BIOEM_ERR_CUDA, "cudaSetDevice");
+    switch (images->nx) {
+        case 32: return run_gathered<C32_4>(ctx, images, projset, max_shift, d_offsets, d_ps_idx, nnz, max_per_image, d_acc, first);
+        case 64: return max_shift <= 4 ? run_gathered<C64_4>(ctx, images, projset, max_shift, d_offsets, d_ps_idx, nnz, max_per_image, d_acc, first)
+                                       : run_gathered<C64_8>(ctx, images, projset, max_shift, d_offsets, d_ps_idx, nnz, max_per_image, d_acc, first);
+        case 96: return run_gathered<C96_12>(ctx, images, projset, max_shift, d_offsets, d_ps_idx, nnz, max_per_image, d_acc, first);
+        case 128: return max_shift <= 4 ? run_gathered<C128_4>(ctx, images, projset, max_shift, d_offsets, d_ps_idx, nnz, max_per_image, d_acc, first)
+                                        : run_gathered<C128_16>(ctx, images, projset, max_shift, d_offsets, d_ps_idx, nnz, max_per_image, d_acc, first);
+        default: return run_gathered<C192_24>(ctx, images, projset, max_shift, d_offsets, d_ps_idx, nnz, max_per_image, d_acc, first);
+    }
+}
+
+int bioem_acc_logP(bioem_ctx* ctx, const double* d_acc, int n_img, double log_norm, double* d_logP) {
+    if (!ctx || (n_img > 0 && (!d_acc || !d_logP)) || n_img < 0) return BIOEM_ERR_INVALID_ARG;
+    if (n_img == 0) return BIOEM_OK;
+    cudaSetDevice(ctx->device);
+    bioem_launch_begin(ctx, KID_FINALIZE);
+    k_acc_logP<<<(n_img + 255) / 256, 256, 0, ctx->stream>>>(d_acc, n_img, log_norm, d_logP);
+    bioem_launch_end(ctx, KID_FINALIZE);
+    return bioem_check_cuda(ctx, cudaGetLastError(), "k_acc_logP");
 }
 
 }  // extern "C"
