@@ -1,0 +1,129 @@
+"""Learned-proposal path: train the network on forward-model projections, propose coarse cells,
+score each image only on the fine parameter sets of its proposed cells.
+
+Orchestration of library calls; every computation runs in the CUDA kernels behind the C ABI
+(synthetic maps, network training / inference / top-k, projection, gathered scoring).  The host
+side builds index lists (which fine parameter sets belong to which proposed cells) and composes
+the synthetic training images from the library's noiseless maps with seeded shifts, scales,
+offsets and noise.
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+
+from . import CNN, Context, acc_logP, prepare_images, project_model, score_gathered, synthetic_maps
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def compose(ctx: Context, atoms_dev: list, d: dict, cfg, gen, out=None):
+    """Images N I1(r + d) - mu + lambda z for the parameter draws d (device float32 [n, N, N])."""
+    torch = _torch()
+    n = len(d["quat"])
+    N = cfg.npix
+    dev = ctx.device
+    if out is None:
+        out = torch.empty((n, N, N), dtype=torch.float32, device=dev)
+    yy = torch.arange(N, device=dev).view(1, N, 1)
+    xx = torch.arange(N, device=dev).view(1, 1, N)
+    chunk = 4096
+    for m in range(len(atoms_dev)):
+        idx_all = np.nonzero(d["model"] == m)[0]
+        for c0 in range(0, len(idx_all), chunk):
+            idx = idx_all[c0:c0 + chunk]
+            q = torch.from_numpy(np.ascontiguousarray(d["quat"][idx])).to(dev)
+            rows = [(d["defocus_A"][i], cfg.amp_contrast, d["bfactor"][i], cfg.voltage_kV) for i in idx]
+            maps = synthetic_maps(ctx, atoms_dev[m], cfg.sigma_A, q, rows, N, cfg.pixel_A)
+            it = torch.from_numpy(idx).to(dev)
+            dy = torch.from_numpy(d["dy"][idx]).to(dev).view(-1, 1, 1)
+            dx = torch.from_numpy(d["dx"][idx]).to(dev).view(-1, 1, 1)
+            b = torch.arange(len(idx), device=dev).view(-1, 1, 1)
+            sig = maps[b, (yy + dy) % N, (xx + dx) % N] * torch.from_numpy(d["norm"][idx]).float().to(dev).view(-1, 1, 1)
+            lam = torch.sqrt(sig.double().var(dim=(1, 2), unbiased=False) / cfg.snr).float().view(-1, 1, 1)
+            z = torch.randn(sig.shape, generator=gen, device=dev)
+            out[it] = sig - torch.from_numpy(d["offset"][idx]).float().to(dev).view(-1, 1, 1) + lam * z
+    return out
+
+
+def train(net: CNN, images, yq, yd, epochs: int, batch: int, lr: float, gen) -> list:
+    """Adam epochs over shuffled mini-batches; mean loss per epoch."""
+    torch = _torch()
+    n = images.shape[0]
+    losses = []
+    for ep in range(epochs):
+        perm = torch.randperm(n, generator=gen, device=images.device)
+        tot = torch.zeros((), dtype=torch.float64, device=images.device)
+        steps = 0
+        for b0 in range(0, n - batch + 1, batch):
+            sel = perm[b0:b0 + batch]
+            loss = net.train_step(images[sel].contiguous(), yq[sel].contiguous(), yd[sel].contiguous(), lr)
+            tot += loss.double().mean()
+            steps += 1
+        losses.append(float(tot.item()) / max(1, steps))
+    return losses
+
+
+def score_cells(ctx: Context, images, atoms_dev, bins: np.ndarray, cfg, wave: int = 256) -> dict:
+    """ln P of every image over the union of its joint cells bins[i] (coarse cell * n_defocus + defocus
+    bin), each cell expanded to its fine orientations x the cell's defocus x every B.  ln P is
+    normalised by the FULL fine grid (n_fine x n_defocus x n_B x S), so cells not scored count as
+    zero likelihood: it equals the full-grid posterior when the cells hold all its mass."""
+    import workloads
+    torch = _torch()
+    dev = ctx.device
+    n_img = bins.shape[0]
+    nd, nb = cfg.n_defocus, len(cfg.bfactors)
+    nctf = nd * nb
+    fine_q = workloads.hopf_grid(cfg.fine_level).astype(np.float32)
+    kids = cfg.children
+    S = (2 * cfg.max_shift + 1) ** 2
+    log_norm = math.log(len(fine_q) * nctf * S)
+    cells = bins // nd
+    used = np.unique(cells)
+    acc = torch.empty((n_img, 2), dtype=torch.float64, device=dev)
+    first = True
+    evals = 0
+    t0 = time.perf_counter()
+    rows = cfg.ctf_rows()
+    for w0 in range(0, len(used), wave):
+        wc = used[w0:w0 + wave]
+        pos = np.full(cfg.n_coarse, -1, dtype=np.int64)
+        pos[wc] = np.arange(len(wc))
+        child = workloads.hopf_children(cfg.coarse_level, cfg.fine_level, wc).ravel()
+        q = torch.from_numpy(np.ascontiguousarray(fine_q[child])).to(dev)
+        ps = project_model(ctx, atoms_dev, cfg.sigma_A, q, rows, cfg.npix, cfg.pixel_A)
+        # per image: the (cell, defocus) bins of this wave -> fine sets (pos * kids + j) * nctf + d * nb + b
+        lists = []
+        for i in range(n_img):
+            sel = bins[i][pos[cells[i]] >= 0]
+            if len(sel) == 0:
+                lists.append(np.zeros(0, dtype=np.int64))
+                continue
+            p = pos[sel // nd]
+            dd = sel % nd
+            j = np.arange(kids)
+            idx = ((p[:, None, None] * kids + j[None, :, None]) * nctf + dd[:, None, None] * nb
+                   + np.arange(nb)[None, None, :])
+            lists.append(idx.ravel())
+        counts = np.array([len(x) for x in lists])
+        evals += int(counts.sum())
+        off = torch.from_numpy(np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)).to(dev)
+        flat = torch.from_numpy(np.concatenate(lists).astype(np.int32)).to(dev)
+        score_gathered(ctx, images, ps, cfg.max_shift, off, flat, max(1, int(counts.max())), acc, first)
+        first = False
+        ps.close()
+    logp = acc_logP(ctx, acc, log_norm)
+    torch.cuda.synchronize()
+    return {"logP": logp.cpu().numpy(), "evals": evals, "seconds": time.perf_counter() - t0,
+            "cells": int(len(used))}
+
+
+def all_bins(n_img: int, cfg) -> np.ndarray:
+    """Every joint bin for every image (the full grid)."""
+    return np.tile(np.arange(cfg.n_coarse * cfg.n_defocus, dtype=np.int64), (n_img, 1))

@@ -1,0 +1,74 @@
+"""GPU: the learned proposal end to end at a small scale, against the full grid and random proposals.
+
+Trains the network (own kernels) on forward-model projections, proposes the top-k joint (coarse
+Hopf cell, defocus) bins of fresh images, scores each image only on its proposed fine parameter
+sets, and compares with the full fine grid (the judge) and with random proposals of the same size:
+the gain of the learned part is the posterior mass it keeps beyond what random cells keep.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1609_06634_gb300 as bioem
+    from paper_1609_06634_gb300 import build
+    build.build()
+    return bioem, bioem.Context(0)
+
+
+def test_proposal_end_to_end(env):
+    import torch
+    bioem, ctx = env
+    from paper_1609_06634_gb300 import proposal
+    cfg = workloads.ProposalConfig(n_models=2, atoms_range=(2000, 3000), npix=64, pixel_A=2.2, max_shift=8,
+                                   coarse_level=1, fine_level=2, top_k=8, n_train=6144, n_infer=40, channels=16)
+    dev = torch.device("cuda", 0)
+    gen = torch.Generator(device=dev).manual_seed(1)
+    atoms = [torch.from_numpy(a).to(dev) for a in workloads.proposal_models(cfg)]
+    tr = workloads.proposal_draws(cfg, cfg.n_train, 8)
+    imgs = proposal.compose(ctx, atoms, tr, cfg, gen)
+    net = bioem.CNN(ctx, image_px=cfg.npix, downsample=cfg.downsample, channels=cfg.channels,
+                    n_qbins=cfg.n_coarse, n_dbins=cfg.n_defocus, max_batch=128, seed=2)
+    losses = proposal.train(net, imgs, torch.from_numpy(tr["label_q"]).to(dev), torch.from_numpy(tr["label_d"]).to(dev),
+                            epochs=4, batch=128, lr=2e-3, gen=gen)
+    assert losses[-1] < losses[0]
+    inf = workloads.proposal_draws(cfg, cfg.n_infer, 9, models=False)
+    x = proposal.compose(ctx, [atoms[0]], inf, cfg, gen)
+    bins, _ = net.propose(x, cfg.top_k)
+    bins = bins.cpu().numpy().astype(np.int64)
+    im = bioem.prepare_images(ctx, x, cfg.pixel_A)
+    rng = np.random.default_rng(3)
+    n_joint = cfg.n_coarse * cfg.n_defocus
+    rand = np.stack([rng.choice(n_joint, cfg.top_k, replace=False) for _ in range(cfg.n_infer)])
+    prop = proposal.score_cells(ctx, im, atoms[0], bins, cfg)
+    rnd = proposal.score_cells(ctx, im, atoms[0], rand, cfg)
+    full = proposal.score_cells(ctx, im, atoms[0], proposal.all_bins(cfg.n_infer, cfg), cfg)
+    assert ctx.status() == 0
+    # subsets of the grid, normalised by the full grid, can only lose mass
+    assert np.all(prop["logP"] <= full["logP"] + 1e-6)
+    assert np.all(rnd["logP"] <= full["logP"] + 1e-6)
+    assert prop["evals"] == cfg.n_infer * cfg.top_k * cfg.children * len(cfg.bfactors)
+    # the wave-gathered full grid equals one bioem_score over the whole fine grid
+    fq = torch.from_numpy(workloads.hopf_grid(cfg.fine_level).astype(np.float32)).to(dev)
+    ps = bioem.project_model(ctx, atoms[0], cfg.sigma_A, fq, cfg.ctf_rows(), cfg.npix, cfg.pixel_A)
+    ref = bioem.score(ctx, im, ps, cfg.max_shift).cpu().numpy()
+    np.testing.assert_allclose(full["logP"], ref, rtol=0, atol=1e-6)
+    # the learned proposal keeps more posterior mass than random cells of the same number
+    kept_prop = prop["logP"] - full["logP"]
+    kept_rand = rnd["logP"] - full["logP"]
+    print(f"losses {losses}; kept (log mass) proposal median {np.median(kept_prop):.3f} mean {np.mean(kept_prop):.3f}; "
+          f"random mean {np.mean(kept_rand):.3f}; evals proposal {prop['evals']} full {full['evals']}")
+    assert np.mean(kept_prop) > np.mean(kept_rand) + 1.0, (np.mean(kept_prop), np.mean(kept_rand))
+    truth = inf["label_q"].astype(np.int64) * cfg.n_defocus + inf["label_d"]
+    recall = np.mean([t in b for t, b in zip(truth, bins)])
+    assert recall > cfg.top_k / n_joint

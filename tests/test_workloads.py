@@ -99,3 +99,34 @@ def test_draws_stable_under_subsetting():
     assert a["ctfs"].shape == (6, 4) and a["quats"].shape == (1152, 4)
     p = workloads.get_config("precision64")
     assert np.array_equal(workloads.workload(p, 1)["quats"], a["quats"])   # reuses the tiny grid
+
+
+def test_healpix_ang2pix_inverts_pix2ang():
+    from workloads.generate import healpix_nest_ang2pix
+    for nside in (1, 2, 4, 16):
+        pix = np.arange(12 * nside * nside)
+        th, ph = healpix_nest_pix2ang(nside, pix)
+        np.testing.assert_array_equal(healpix_nest_ang2pix(nside, th, ph), pix)
+    # random directions land in the pixel whose children (next level) contain them
+    rng = np.random.default_rng(0)
+    v = rng.standard_normal((2000, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    th, ph = np.arccos(v[:, 2]), np.arctan2(v[:, 1], v[:, 0])
+    np.testing.assert_array_equal(healpix_nest_ang2pix(8, th, ph) >> 2, healpix_nest_ang2pix(4, th, ph))
+    # equal areas: uniform directions fill the 192 pixels evenly
+    counts = np.bincount(healpix_nest_ang2pix(4, th, ph), minlength=192)
+    assert counts.min() > 0 and counts.max() < 3 * 2000 / 192
+
+
+def test_hopf_cell_and_children():
+    for level in (0, 1, 2):
+        q = workloads.hopf_grid(level)
+        np.testing.assert_array_equal(workloads.hopf_cell(level, q), np.arange(len(q)))
+        np.testing.assert_array_equal(workloads.hopf_cell(level, -q), np.arange(len(q)))
+    fine = workloads.hopf_grid(3)
+    kids = workloads.hopf_children(1, 3, np.arange(576))
+    assert kids.shape == (576, 64)
+    np.testing.assert_array_equal(np.sort(kids.ravel()), np.arange(len(fine)))
+    np.testing.assert_array_equal(workloads.hopf_coarse_index(3, 1, kids), np.repeat(np.arange(576), 64).reshape(576, 64))
+    # a fine point's cell at the coarse level is its parent
+    np.testing.assert_array_equal(workloads.hopf_cell(1, fine), workloads.hopf_coarse_index(3, 1, np.arange(len(fine))))

@@ -15,11 +15,15 @@ are those of the configurations in ``configs.py`` and ``batched.py``.
 """
 from .configs import CONFIGS, Config, get_config  # noqa: F401
 from .batched import BatchedConfig, StackSpec, batched_workload, model_atoms  # noqa: F401
+from .proposal import ProposalConfig, draws as proposal_draws, proposal_models  # noqa: F401
 from .generate import (  # noqa: F401
     atoms_in_ball,
     ctf_grid,
     defocus_grid,
+    healpix_nest_ang2pix,
     healpix_nest_pix2ang,
+    hopf_cell,
+    hopf_children,
     hopf_grid,
     hopf_coarse_index,
     image_truth,

@@ -75,6 +75,79 @@ def healpix_nest_pix2ang(nside: int, ipix: np.ndarray) -> tuple[np.ndarray, np.n
     return theta, phi
 
 
+def _spread_bits(v: np.ndarray) -> np.ndarray:
+    """Place the bits of v on the even bit positions."""
+    out = np.zeros_like(v)
+    for b in range(32):
+        out |= ((v >> b) & 1) << (2 * b)
+    return out
+
+
+def healpix_nest_ang2pix(nside: int, theta: np.ndarray, phi: np.ndarray) -> np.ndarray:
+    """NESTED HEALPix pixel containing each direction (Gorski et al. 2005), inverse of pix2ang."""
+    z = np.cos(np.asarray(theta, dtype=np.float64))
+    za = np.abs(z)
+    tt = np.mod(np.asarray(phi, dtype=np.float64), 2.0 * math.pi) * (2.0 / math.pi)   # in [0, 4)
+    ipix = np.empty(z.shape, dtype=np.int64)
+    eq = za <= 2.0 / 3.0
+    # equatorial region
+    t1 = nside * (0.5 + tt[eq])
+    t2 = nside * z[eq] * 0.75
+    jp = (t1 - t2).astype(np.int64)
+    jm = (t1 + t2).astype(np.int64)
+    ifp, ifm = jp // nside, jm // nside
+    face = np.where(ifp == ifm, ifp | 4, np.where(ifp < ifm, ifp, ifm + 8))
+    ix = jm & (nside - 1)
+    iy = nside - (jp & (nside - 1)) - 1
+    ipix[eq] = face * nside * nside + _spread_bits(ix) + (_spread_bits(iy) << 1)
+    # polar caps
+    pc = ~eq
+    ntt = np.minimum(3, tt[pc].astype(np.int64))
+    tp = tt[pc] - ntt
+    tmp = nside * np.sqrt(3.0 * (1.0 - za[pc]))
+    jp = np.minimum((tp * tmp).astype(np.int64), nside - 1)
+    jm = np.minimum(((1.0 - tp) * tmp).astype(np.int64), nside - 1)
+    north = z[pc] >= 0
+    face = np.where(north, ntt, ntt + 8)
+    ix = np.where(north, nside - jm - 1, jp)
+    iy = np.where(north, nside - jp - 1, jm)
+    ipix[pc] = face * nside * nside + _spread_bits(ix) + (_spread_bits(iy) << 1)
+    return ipix
+
+
+def hopf_cell(level: int, quats: np.ndarray) -> np.ndarray:
+    """Index of the Hopf-grid cell (level) containing each unit quaternion (w, x, y, z); q and -q agree.
+
+    Inverts q = (cos(t/2) cos(p/2), cos(t/2) sin(p/2), sin(t/2) cos(f + p/2), sin(t/2) sin(f + p/2)):
+    t = 2 atan2(|(y, z)|, |(w, x)|), psi = 2 atan2(x, w) mod 2 pi, phi = atan2(z, y) - psi/2 mod 2 pi.
+    """
+    q = np.asarray(quats, dtype=np.float64)
+    q = q / np.linalg.norm(q, axis=1, keepdims=True)
+    # sign convention: the half angle psi/2 = atan2(x, w) in [0, pi) (q -> -q shifts it by pi)
+    half = np.arctan2(q[:, 1], q[:, 0])
+    q = np.where(((half < 0.0) | (half >= math.pi))[:, None], -q, q)
+    half = np.mod(np.arctan2(q[:, 1], q[:, 0]), math.pi)
+    theta = 2.0 * np.arctan2(np.hypot(q[:, 2], q[:, 3]), np.hypot(q[:, 0], q[:, 1]))
+    psi = 2.0 * half
+    phi = np.mod(np.arctan2(q[:, 3], q[:, 2]) - half, 2.0 * math.pi)
+    nside = 2 ** level
+    n_psi = 6 * 2 ** level
+    pix = healpix_nest_ang2pix(nside, theta, phi)
+    k = np.minimum((psi / (2.0 * math.pi) * n_psi).astype(np.int64), n_psi - 1)
+    return pix * n_psi + k
+
+
+def hopf_children(coarse_level: int, fine_level: int, coarse_index: np.ndarray) -> np.ndarray:
+    """[n, 8**(fine - coarse)] fine-grid indices of the cells nested in each coarse cell."""
+    d = fine_level - coarse_level
+    n_psi_c, n_psi_f = 6 * 2 ** coarse_level, 6 * 2 ** fine_level
+    c = np.asarray(coarse_index, dtype=np.int64)
+    pix, k = c // n_psi_c, c % n_psi_c
+    sub_pix = (pix[:, None] << (2 * d)) + np.arange(4 ** d)[None, :]          # [n, 4^d]
+    sub_k = (k[:, None] << d) + np.arange(2 ** d)[None, :]                      # [n, 2^d]
+    return (sub_pix[:, :, None] * n_psi_f + sub_k[:, None, :]).reshape(len(c), -1)
+
+
 def hopf_grid(level: int) -> np.ndarray:
     """[72 * 8**level, 4] float64 unit quaternions of the Hopf-fibration grid (Yershova et al. 2010).
 
