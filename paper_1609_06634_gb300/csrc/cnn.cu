@@ -429,6 +429,8 @@ int grid_for(size_t n) {
 
 struct bioem_cnn {
     bioem_ctx* ctx;
+    int device;            // bioem_cnn_free uses these, never the (possibly destroyed) context
+    cudaStream_t stream;
     int S, C, n_q, n_d, max_batch, down, n_in;
     Layer layers[kLayers];
     size_t n_params, F;
@@ -561,6 +563,8 @@ int bioem_cnn_create(bioem_ctx* ctx, int image_px, int downsample, int channels,
     bioem_cnn* n = new (std::nothrow) bioem_cnn();
     if (!n) return BIOEM_ERR_OOM;
     n->ctx = ctx;
+    n->device = ctx->device;
+    n->stream = ctx->stream;
     n->n_in = image_px;
     n->down = downsample;
     n->S = image_px / downsample;
@@ -721,8 +725,8 @@ int bioem_propose(bioem_cnn* n, const float* d_images, int n_img, int k, int* d_
 
 void bioem_cnn_free(bioem_cnn* n) {
     if (!n) return;
-    cudaSetDevice(n->ctx->device);
-    cudaStreamSynchronize(n->ctx->stream);
+    cudaSetDevice(n->device);
+    cudaStreamSynchronize(n->stream);
     cudaFree(n->d_p);
     cudaFree(n->d_p16);
     cudaFree(n->d_g);

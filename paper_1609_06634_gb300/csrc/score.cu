@@ -948,6 +948,8 @@ int multi_smax(int npix) {
 
 struct bioem_batch {
     bioem_ctx* ctx;
+    int device;            // bioem_batch_free uses these, never the (possibly destroyed) context
+    cudaStream_t stream;
     int n_models, n_stacks, n_cols;
     std::vector<SegDesc> segs;
     SegDesc* d_segs;
@@ -1126,6 +1128,8 @@ int bioem_batch_create(bioem_ctx* ctx, int n_models, int n_stacks, const bioem_i
     bioem_batch* b = new (std::nothrow) bioem_batch();
     if (!b) return BIOEM_ERR_OOM;
     b->ctx = ctx;
+    b->device = ctx->device;
+    b->stream = ctx->stream;
     b->n_models = n_models;
     b->n_stacks = n_stacks;
     b->d_out = d_logP_matrix;
@@ -1230,8 +1234,8 @@ long long bioem_batch_evals(const bioem_batch* b) {
 
 void bioem_batch_free(bioem_batch* b) {
     if (!b) return;
-    cudaSetDevice(b->ctx->device);
-    cudaStreamSynchronize(b->ctx->stream);
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);

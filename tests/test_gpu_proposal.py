@@ -27,11 +27,14 @@ def env():
 
 
 def test_proposal_end_to_end(env):
+    """Scaled down so that a short training run learns: one model, 72 coarse cells (Hopf level 0) of
+    8 fine orientations each, 64 px images, SNR 1.  The full-scale workload is measured by bench.py."""
     import torch
     bioem, ctx = env
     from paper_1609_06634_gb300 import proposal
-    cfg = workloads.ProposalConfig(n_models=2, atoms_range=(2000, 3000), npix=64, pixel_A=2.2, max_shift=8,
-                                   coarse_level=1, fine_level=2, top_k=8, n_train=6144, n_infer=40, channels=16)
+    cfg = workloads.ProposalConfig(n_models=1, atoms_range=(3000, 3000), npix=64, pixel_A=2.2, max_shift=8,
+                                   coarse_level=0, fine_level=1, top_k=8, n_train=12288, n_infer=40, channels=16,
+                                   snr=1.0)
     dev = torch.device("cuda", 0)
     gen = torch.Generator(device=dev).manual_seed(1)
     atoms = [torch.from_numpy(a).to(dev) for a in workloads.proposal_models(cfg)]
@@ -40,7 +43,7 @@ def test_proposal_end_to_end(env):
     net = bioem.CNN(ctx, image_px=cfg.npix, downsample=cfg.downsample, channels=cfg.channels,
                     n_qbins=cfg.n_coarse, n_dbins=cfg.n_defocus, max_batch=128, seed=2)
     losses = proposal.train(net, imgs, torch.from_numpy(tr["label_q"]).to(dev), torch.from_numpy(tr["label_d"]).to(dev),
-                            epochs=4, batch=128, lr=2e-3, gen=gen)
+                            epochs=8, batch=128, lr=2e-3, gen=gen)
     assert losses[-1] < losses[0]
     inf = workloads.proposal_draws(cfg, cfg.n_infer, 9, models=False)
     x = proposal.compose(ctx, [atoms[0]], inf, cfg, gen)
