@@ -445,8 +445,85 @@ def bench_batched(args):
     return 0
 
 
+def bench_proposal(args):
+    """Learned proposal at the configuration's scale: train on 200k forward-model projections of 10
+    models, propose the top-32 joint (coarse Hopf cell, defocus) bins for 10,000 images, score them on
+    their fine parameter sets; judge against the full fine grid on a subset of the images."""
+    import torch
+
+    import paper_1609_06634_gb300 as bioem
+    from paper_1609_06634_gb300 import build, proposal
+
+    build.build()
+    dev = torch.device("cuda", 0)
+    cfg = workloads.ProposalConfig()
+    if args.n_img:
+        cfg = workloads.ProposalConfig(n_infer=args.n_img)
+    n_judge = 32
+    ctx = bioem.Context(0)
+    gen = torch.Generator(device=dev).manual_seed(5)
+    t0 = time.perf_counter()
+    atoms = [torch.from_numpy(a).to(dev) for a in workloads.proposal_models(cfg)]
+    tr = workloads.proposal_draws(cfg, cfg.n_train, 8)
+    imgs = proposal.compose(ctx, atoms, tr, cfg, gen)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    net = bioem.CNN(ctx, image_px=cfg.npix, downsample=cfg.downsample, channels=cfg.channels, n_qbins=cfg.n_coarse,
+                    n_dbins=cfg.n_defocus, max_batch=256, seed=11)
+    t0 = time.perf_counter()
+    epochs = 3
+    losses = proposal.train(net, imgs, torch.from_numpy(tr["label_q"]).to(dev), torch.from_numpy(tr["label_d"]).to(dev),
+                            epochs=epochs, batch=256, lr=1e-3, gen=gen)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del imgs
+    inf = workloads.proposal_draws(cfg, cfg.n_infer, 9, models=False)
+    x = proposal.compose(ctx, [atoms[0]], inf, cfg, gen)
+    im = bioem.prepare_images(ctx, x, cfg.pixel_A)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bins, _ = net.propose(x, cfg.top_k)
+    bins = bins.cpu().numpy().astype(np.int64)
+    t_prop = time.perf_counter() - t0
+    res = proposal.score_cells(ctx, im, atoms[0], bins, cfg)
+    truth = inf["label_q"].astype(np.int64) * cfg.n_defocus + inf["label_d"]
+    recall = float(np.mean([t in b for t, b in zip(truth, bins)]))
+    # judge: the full fine grid on the first n_judge images, and random proposals of the same size
+    jx = x[:n_judge].contiguous()
+    jim = bioem.prepare_images(ctx, jx, cfg.pixel_A)
+    full = proposal.score_cells(ctx, jim, atoms[0], proposal.all_bins(n_judge, cfg), cfg)
+    rng = np.random.default_rng(3)
+    rand = np.stack([rng.choice(cfg.n_coarse * cfg.n_defocus, cfg.top_k, replace=False) for _ in range(n_judge)])
+    rnd = proposal.score_cells(ctx, jim, atoms[0], rand, cfg)
+    kept = res["logP"][:n_judge] - full["logP"]
+    kept_rand = rnd["logP"] - full["logP"]
+    per_img_prop = (t_prop + res["seconds"]) / cfg.n_infer
+    per_img_full = full["seconds"] / n_judge
+    line = {"metric": METRIC, "value": res["evals"] / res["seconds"], "unit": UNIT, "n_gpus": 1, "steps": 1,
+            "warmup": 0, "ms_per_step": res["seconds"] * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "learned proposal: 10 models (2000-10000 atoms), 200k training projections "
+                                   "(128 px, SNR 0.1), 10,000 inference images of model 0, top-32 of 4608 coarse "
+                                   "Hopf cells x 4 defocus bins, each expanded to 64 fine orientations (Hopf level 4, "
+                                   "294,912) x 2 B", "n_infer": cfg.n_infer, "n_judge": n_judge,
+                       "epochs": epochs, "train_images": cfg.n_train},
+            "proposal": {"train_loss_per_epoch": losses, "data_s": t_data, "train_s": t_train, "propose_s": t_prop,
+                         "recall_at_k_true_joint_bin": recall, "random_recall": cfg.top_k / (cfg.n_coarse * cfg.n_defocus),
+                         "evals_per_image": res["evals"] / cfg.n_infer, "full_evals_per_image": full["evals"] / n_judge,
+                         "kept_log_mass_median": float(np.median(kept)), "kept_log_mass_mean": float(np.mean(kept)),
+                         "dlogP_max_vs_full": float(np.max(np.abs(kept))),
+                         "random_kept_log_mass_mean": float(np.mean(kept_rand)),
+                         "seconds_per_image_proposal": per_img_prop, "seconds_per_image_full": per_img_full,
+                         "speedup_vs_full_grid": per_img_full / per_img_prop, "cells_projected": res["cells"]}}
+    print(json.dumps(line), flush=True)
+    net.close()
+    return 0
+
+
 def main():
     args = parse_args()
+    if args.workload == "proposal":
+        return bench_proposal(args)
     if args.impl == "reference":
         return bench_reference(args)
     if args.workload == "batched":
