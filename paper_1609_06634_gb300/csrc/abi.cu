@@ -259,6 +259,7 @@ int bioem_prepare_images(bioem_ctx* ctx, const float* d_images, int n_img, int n
     im->pixel_A = pixel_A;
     int rc = alloc(ctx, &im->d_spec, (size_t)n_img * ny * (nx / 2 + 1), "image spectra");
     if (!rc) rc = alloc(ctx, &im->d_kA, (size_t)n_img, "image constants");
+    if (!rc) rc = alloc(ctx, &im->d_amax, (size_t)n_img, "image constants");
     if (!rc && n_img > 0) rc = bioem_launch_prepare(ctx, d_images, im);
     if (rc) {
         bioem_free_images(im);
@@ -299,6 +300,7 @@ int bioem_project_model(bioem_ctx* ctx, const float* d_atoms, int n_atoms, doubl
     ps->pixel_A = pixel_A;
     int rc = alloc(ctx, &ps->d_spec, (size_t)ps->n_ps * ny * (nx / 2 + 1), "projection spectra");
     if (!rc) rc = alloc(ctx, &ps->d_kB, (size_t)ps->n_ps, "projection constants");
+    if (!rc) rc = alloc(ctx, &ps->d_amax, (size_t)ps->n_ps, "projection constants");
     if (!rc && nq > 0) rc = bioem_launch_project(ctx, d_atoms, n_atoms, sigma_A, d_quats, nq, ctfs, nctf, ps);
     if (rc) {
         bioem_free_projset(ps);
@@ -392,6 +394,7 @@ void bioem_free_images(bioem_images* im) {
     cudaSetDevice(im->device);
     release(im->stream, im->d_spec);
     release(im->stream, im->d_kA);
+    release(im->stream, im->d_amax);
     free(im);
 }
 
@@ -400,6 +403,7 @@ void bioem_free_projset(bioem_projset* ps) {
     cudaSetDevice(ps->device);
     release(ps->stream, ps->d_spec);
     release(ps->stream, ps->d_kB);
+    release(ps->stream, ps->d_amax);
     free(ps);
 }
 

@@ -52,6 +52,7 @@ struct bioem_images {
     double pixel_A;
     float2* d_spec;   // [n_img][ny][nx/2 + 1] unit-norm half spectrum, DC = 0
     double* d_kA;     // [n_img] (3-n)/2 ln A + c(n)
+    float* d_amax;    // [n_img] largest |coefficient| of the stored spectrum
 };
 
 struct bioem_projset {
@@ -62,6 +63,7 @@ struct bioem_projset {
     double pixel_A;
     float2* d_spec;   // [n_ps][ny][nx/2 + 1] unit-norm PSF-filtered projection spectrum, DC = 0
     double* d_kB;     // [n_ps] -1/2 ln B
+    float* d_amax;    // [n_ps] largest |coefficient| of the stored spectrum
 };
 
 // ------------------------------------------------------------------ status codes inside kernels

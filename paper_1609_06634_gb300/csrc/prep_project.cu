@@ -115,18 +115,30 @@ __device__ void load_twiddles(const float2* __restrict__ g_tw, float2* tw) {
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = g_tw[i];
 }
 
-// Write F * T * scale (DC zeroed) to a [N][N/2 + 1] half spectrum.
+// Write F * T * scale (DC zeroed) to a [N][N/2 + 1] half spectrum; returns (to thread 0) the largest
+// |coefficient| written (block reduction over red, which must hold blockDim.x floats).
 template <int N>
-__device__ void store_half_spectrum(const float2* F, const float* __restrict__ T, float scale,
-                                    float2* __restrict__ spec) {
+__device__ float store_half_spectrum(const float2* F, const float* __restrict__ T, float scale,
+                                     float2* __restrict__ spec, float* red) {
     constexpr int H = N / 2 + 1;
+    float amax = 0.f;
     for (int o = threadIdx.x; o < N * H; o += blockDim.x) {
         float2 v = F[o];
         if (T) v = c_scale(v, T[o]);
         v = c_scale(v, scale);
         if (o == 0) v = make_float2(0.f, 0.f);
         spec[o] = v;
+        amax = fmaxf(amax, fmaxf(fabsf(v.x), fabsf(v.y)));
     }
+    red[threadIdx.x] = amax;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + st]);
+        __syncthreads();
+    }
+    const float r = red[0];
+    __syncthreads();
+    return r;
 }
 
 // sum over k != 0 of w_kx |F T|^2 over the full spectrum (w = 1 on the kx = 0 and N/2 columns,
@@ -151,7 +163,8 @@ template <int N>
 __global__ void __launch_bounds__(kThreads) k_prepare_images(const float* __restrict__ images,
                                                               const float2* __restrict__ g_tw,
                                                               float2* __restrict__ spec,
-                                                              double* __restrict__ kA, double cn,
+                                                              double* __restrict__ kA, float* __restrict__ amax,
+                                                              double cn,
                                                               int* __restrict__ status) {
     constexpr int H = N / 2 + 1;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -179,8 +192,9 @@ __global__ void __launch_bounds__(kThreads) k_prepare_images(const float* __rest
     const double e = half_spectrum_energy<N>(F, nullptr, red);
     const bool bad = !(A > 0.0) || !(e > 0.0);
     const float scale = bad ? 0.f : (float)(1.0 / sqrt(e));
-    store_half_spectrum<N>(F, nullptr, scale, spec + (size_t)w * N * H);
+    const float mx = store_half_spectrum<N>(F, nullptr, scale, spec + (size_t)w * N * H, reinterpret_cast<float*>(red));
     if (threadIdx.x == 0) {
+        amax[w] = mx;
         if (bad) {
             atomicOr(status, BIOEM_DEV_NUMERIC);
             kA[w] = -INFINITY;
@@ -337,7 +351,7 @@ __global__ void __launch_bounds__(kThreads) k_psf_spectra(const float* __restric
                                                            const float2* __restrict__ g_tw,
                                                            const float* __restrict__ T, int nctf,
                                                            float2* __restrict__ spec,
-                                                           double* __restrict__ kB,
+                                                           double* __restrict__ kB, float* __restrict__ amax,
                                                            int* __restrict__ status) {
     constexpr int H = N / 2 + 1;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -355,8 +369,10 @@ __global__ void __launch_bounds__(kThreads) k_psf_spectra(const float* __restric
         const double B = half_spectrum_energy<N>(F, Tc, red);   // n C_cc - C_c^2 (Plancherel)
         const bool bad = !(B > 0.0);
         const size_t p = (size_t)q * nctf + c;
-        store_half_spectrum<N>(F, Tc, bad ? 0.f : (float)(1.0 / sqrt(B)), spec + p * N * H);
+        const float mx = store_half_spectrum<N>(F, Tc, bad ? 0.f : (float)(1.0 / sqrt(B)), spec + p * N * H,
+                                                reinterpret_cast<float*>(red));
         if (threadIdx.x == 0) {
+            amax[p] = mx;
             if (bad) {
                 atomicOr(status, BIOEM_DEV_NUMERIC);
                 kB[p] = -INFINITY;
@@ -465,7 +481,7 @@ int launch_prepare_n(bioem_ctx* ctx, const float* d_images, bioem_images* im) {
     const double cn = bioem_log_norm_constant(N * N);
     bioem_launch_begin(ctx, KID_PREPARE);
     k_prepare_images<N><<<im->n_img, kThreads, sm, ctx->stream>>>(d_images, bioem_twiddles(ctx, N), im->d_spec,
-                                                                    im->d_kA, cn, ctx->d_status);
+                                                                    im->d_kA, im->d_amax, cn, ctx->d_status);
     bioem_launch_end(ctx, KID_PREPARE);
     return bioem_check_cuda(ctx, cudaGetLastError(), "k_prepare_images");
 }
@@ -499,7 +515,7 @@ int launch_project_n(bioem_ctx* ctx, const float* d_atoms, int n_atoms, double s
         bioem_launch_begin(ctx, KID_PSF_SPECTRA);
         k_psf_spectra<N><<<nb, kThreads, sm, ctx->stream>>>(d_I0, bioem_twiddles(ctx, N), d_T, nctf,
                                                              ps->d_spec + p0 * N * (N / 2 + 1), ps->d_kB + p0,
-                                                             ctx->d_status);
+                                                             ps->d_amax + p0, ctx->d_status);
         bioem_launch_end(ctx, KID_PSF_SPECTRA);
         rc = bioem_check_cuda(ctx, cudaGetLastError(), "k_psf_spectra");
     }

@@ -228,6 +228,102 @@ __device__ __forceinline__ float loglik_t(float rho, int* status) {
     return log1pf(-r2);
 }
 
+// Stage B (row transforms), the dy = +SMAX row, the likelihood epilogue and the per-pair combine of
+// one batch whose Q (stage-A output, [pair][dy][kx]) is in q_s; records for pairs p0 .. hi-1.
+template <class C>
+__device__ __forceinline__ void score_tail(const float2* __restrict__ q_s, const float2* __restrict__ twc_s,
+                                           float* row_t, float* row_s, int* row_d, float* dir_t,
+                                           const float2* __restrict__ gtw, int p0, int hi, int s, float c1,
+                                           float* __restrict__ rec_t, float* __restrict__ rec_s,
+                                           int* __restrict__ rec_d, int* __restrict__ status) {
+    constexpr int N = C::N, NC = C::NC, NS = C::NS, SMAX = C::SMAX, NROW = C::NROW;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const bool active = tid < C::THREADS;
+    // ---------------- stage B: one row (dy = -SMAX .. SMAX-1) of one pair per thread
+    if (tid < C::PB * NROW) {
+        const int j = tid / NROW;
+        const int r = tid - j * NROW;
+        const float2* qrow = q_s + ((size_t)j * NS + r) * C::QS;
+        float acc[NS];
+#pragma unroll
+        for (int m = 0; m < NS; ++m) acc[m] = 0.f;
+        stage_b_row<C>(acc, qrow, twc_s);
+        const float qn = qrow[NC].x;   // Nyquist column, weight 1, phase (-1)^dx
+        const bool row_ok = abs(r - SMAX) <= s;
+        float tmin = INFINITY;
+        int arg = 0x7fffffff;
+#pragma unroll
+        for (int m = 0; m < NS; ++m) {
+            const float rho = acc[m] + (((m - SMAX) & 1) ? -qn : qn);
+            const bool ok = row_ok && abs(m - SMAX) <= s;
+            const float t = ok ? loglik_t(rho, status) : INFINITY;
+            acc[m] = t;
+            if (t < tmin) {
+                tmin = t;
+                arg = r * NS + m;
+            }
+        }
+        float ssum = 0.f;
+#pragma unroll
+        for (int m = 0; m < NS; ++m) ssum += (acc[m] < INFINITY) ? __expf(c1 * (acc[m] - tmin)) : 0.f;
+        row_t[tid] = tmin;
+        row_s[tid] = ssum;
+        row_d[tid] = arg;
+    }
+    // ---------------- the dy = +SMAX row, one output per task, evaluated directly; the
+    // threads without a stage-B row (tid >= PB NROW) take the first outputs so that few
+    // threads with a row get two
+    if (active) {
+#pragma unroll 1
+        for (int i = (tid + C::THREADS - C::PB * NROW) % C::THREADS; i < C::NDIR; i += C::THREADS) {
+            const int j = i / NS;
+            const int mi = i - j * NS;
+            const int dx = mi - SMAX;
+            const float2* qrow = q_s + ((size_t)j * NS + 2 * SMAX) * C::QS;
+            float accv = 0.f;
+            int idx = pmod(dx, N);
+            const int step = idx;
+            for (int kx = 1; kx < NC; ++kx) {
+                const float2 v = qrow[kx];
+                const float2 wv = __ldg(gtw + idx);   // exp(-i theta): Re(v exp(+i theta)) = v.x w.x + v.y w.y
+                accv = fmaf(v.x, wv.x, fmaf(v.y, wv.y, accv));
+                idx += step;
+                idx -= (idx >= N) ? N : 0;
+            }
+            const float rho = qrow[0].x + 2.f * accv + ((dx & 1) ? -qrow[NC].x : qrow[NC].x);
+            const bool ok = SMAX <= s && abs(dx) <= s;
+            dir_t[i] = ok ? loglik_t(rho, status) : INFINITY;
+        }
+    }
+    __syncthreads();
+    // ---------------- combine the pieces of each pair (one full warp per pair)
+    for (int j = warp; warp < C::NWARPS && j < C::PB; j += C::NWARPS) {
+        const int p = p0 + j;
+        if (p >= hi) continue;
+        Part acc{INFINITY, 0.f, 0x7fffffff};
+        for (int r = lane; r < NROW; r += 32)
+            acc = merge(acc, Part{row_t[j * NROW + r], row_s[j * NROW + r], row_d[j * NROW + r]}, c1);
+        for (int mi = lane; mi < NS; mi += 32) {
+            const float t = dir_t[j * NS + mi];
+            acc = merge(acc, Part{t, t < INFINITY ? 1.f : 0.f, 2 * SMAX * NS + mi}, c1);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            Part o;
+            o.t = __shfl_xor_sync(0xffffffffu, acc.t, off);
+            o.s = __shfl_xor_sync(0xffffffffu, acc.s, off);
+            o.d = __shfl_xor_sync(0xffffffffu, acc.d, off);
+            acc = merge(acc, o, c1);   // merge orders its operands, so both lanes agree
+        }
+        if (lane == 0) {
+            rec_t[p] = acc.t;
+            rec_s[p] = acc.s;
+            rec_d[p] = acc.d;
+        }
+    }
+}
+
 // One work item: image w against parameter sets [lo, hi) of the wave starting at ps_begin.
 // img: the image's spectrum; rec_*: the image's record row (indexed by the wave-relative set);
 // gtw: exp(-2 pi i t / N), t < N, in global memory (the direct row's twiddles, L1-resident).
@@ -282,88 +378,7 @@ __device__ __forceinline__ void score_item(unsigned char* smem, const float2* __
             }
         }
         __syncthreads();
-        // ---------------- stage B: one row (dy = -SMAX .. SMAX-1) of one pair per thread
-        if (tid < C::PB * NROW) {
-            const int j = tid / NROW;
-            const int r = tid - j * NROW;
-            const float2* qrow = q_s + ((size_t)j * NS + r) * C::QS;
-            float acc[NS];
-#pragma unroll
-            for (int m = 0; m < NS; ++m) acc[m] = 0.f;
-            stage_b_row<C>(acc, qrow, twc_s);
-            const float qn = qrow[NC].x;   // Nyquist column, weight 1, phase (-1)^dx
-            const bool row_ok = abs(r - SMAX) <= s;
-            float tmin = INFINITY;
-            int arg = 0x7fffffff;
-#pragma unroll
-            for (int m = 0; m < NS; ++m) {
-                const float rho = acc[m] + (((m - SMAX) & 1) ? -qn : qn);
-                const bool ok = row_ok && abs(m - SMAX) <= s;
-                const float t = ok ? loglik_t(rho, status) : INFINITY;
-                acc[m] = t;
-                if (t < tmin) {
-                    tmin = t;
-                    arg = r * NS + m;
-                }
-            }
-            float ssum = 0.f;
-#pragma unroll
-            for (int m = 0; m < NS; ++m) ssum += (acc[m] < INFINITY) ? __expf(c1 * (acc[m] - tmin)) : 0.f;
-            row_t[tid] = tmin;
-            row_s[tid] = ssum;
-            row_d[tid] = arg;
-        }
-        // ---------------- the dy = +SMAX row, one output per task, evaluated directly; the
-        // threads without a stage-B row (tid >= PB NROW) take the first outputs so that few
-        // threads with a row get two
-        if (active) {
-#pragma unroll 1
-            for (int i = (tid + C::THREADS - C::PB * NROW) % C::THREADS; i < C::NDIR; i += C::THREADS) {
-                const int j = i / NS;
-                const int mi = i - j * NS;
-                const int dx = mi - SMAX;
-                const float2* qrow = q_s + ((size_t)j * NS + 2 * SMAX) * C::QS;
-                float accv = 0.f;
-                int idx = pmod(dx, N);
-                const int step = idx;
-                for (int kx = 1; kx < NC; ++kx) {
-                    const float2 v = qrow[kx];
-                    const float2 wv = __ldg(gtw + idx);   // exp(-i theta): Re(v exp(+i theta)) = v.x w.x + v.y w.y
-                    accv = fmaf(v.x, wv.x, fmaf(v.y, wv.y, accv));
-                    idx += step;
-                    idx -= (idx >= N) ? N : 0;
-                }
-                const float rho = qrow[0].x + 2.f * accv + ((dx & 1) ? -qrow[NC].x : qrow[NC].x);
-                const bool ok = SMAX <= s && abs(dx) <= s;
-                dir_t[i] = ok ? loglik_t(rho, status) : INFINITY;
-            }
-        }
-        __syncthreads();
-        // ---------------- combine the pieces of each pair (one full warp per pair)
-        for (int j = warp; warp < C::NWARPS && j < C::PB; j += C::NWARPS) {
-            const int p = p0 + j;
-            if (p >= hi) continue;
-            Part acc{INFINITY, 0.f, 0x7fffffff};
-            for (int r = lane; r < NROW; r += 32)
-                acc = merge(acc, Part{row_t[j * NROW + r], row_s[j * NROW + r], row_d[j * NROW + r]}, c1);
-            for (int mi = lane; mi < NS; mi += 32) {
-                const float t = dir_t[j * NS + mi];
-                acc = merge(acc, Part{t, t < INFINITY ? 1.f : 0.f, 2 * SMAX * NS + mi}, c1);
-            }
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                Part o;
-                o.t = __shfl_xor_sync(0xffffffffu, acc.t, off);
-                o.s = __shfl_xor_sync(0xffffffffu, acc.s, off);
-                o.d = __shfl_xor_sync(0xffffffffu, acc.d, off);
-                acc = merge(acc, o, c1);   // merge orders its operands, so both lanes agree
-            }
-            if (lane == 0) {
-                rec_t[p] = acc.t;
-                rec_s[p] = acc.s;
-                rec_d[p] = acc.d;
-            }
-        }
+        score_tail<C>(q_s, twc_s, row_t, row_s, row_d, dir_t, gtw, p0, hi, s, c1, rec_t, rec_s, rec_d, status);
     }
 }
 
