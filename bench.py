@@ -520,6 +520,105 @@ def bench_proposal(args):
     return 0
 
 
+def bench_precision(args):
+    """Split-precision forms against the FP32 form on the precision workloads: the tiny grid (1152
+    random orientations x 3 defocus x 2 B = 6912 parameter sets), shifts +-4, 64 images of the
+    throughput model at 128 x 128 px (1.1 A) and at 64 x 64 px (2.2 A).  One step = one bioem_score
+    pass over the resident images and projection set; the split-precision operand copies are built
+    once per handle (in warm-up; their build time is reported separately).  |d log P| of each form
+    against the FP64 oracle on these inputs is measured by tests/test_gpu_precision.py."""
+    import torch
+
+    import paper_1609_06634_gb300 as bioem
+    from paper_1609_06634_gb300 import build
+
+    build.build()
+    dev = torch.device("cuda", 0)
+    ctx = bioem.Context(0)
+    stream = torch.cuda.current_stream(dev)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak_tf = peaks.get("bf16_tflops", 1900.0)
+    sizes = {}
+    launches = 0
+    with ClockSampler(None) as clocks:
+        for name in ("precision128", "precision64"):
+            cfg = workloads.get_config(name)
+            n_img = args.n_img or cfg.n_img
+            wl = workloads.workload(cfg, n_img=0)
+            quats_np = wl["quats"] if args.n_quat is None else wl["quats"][:args.n_quat]
+            n_ps = len(quats_np) * len(wl["ctfs"])
+            atoms_d = torch.from_numpy(wl["atoms"]).to(dev)
+            imgs = synth_images(bioem, ctx, cfg, atoms_d, 0, n_img)
+            im = bioem.prepare_images(ctx, imgs, cfg.pixel_A)
+            ps = bioem.project_model(ctx, atoms_d, cfg.sigma_A, torch.from_numpy(np.ascontiguousarray(quats_np)).to(dev),
+                                     wl["ctfs"], cfg.npix, cfg.pixel_A)
+            logp = torch.empty(n_img, dtype=torch.float64, device=dev)
+            forms = {}
+            for mode in ("fp32", "bf16x2", "fp16x2"):
+                ctx.set_precision(mode)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                bioem.score(ctx, im, ps, cfg.max_shift, out=logp)   # builds the operands in a tensor form
+                torch.cuda.synchronize()
+                first_s = time.perf_counter() - t0
+                for _ in range(args.warmup):
+                    bioem.score(ctx, im, ps, cfg.max_shift, out=logp)
+                torch.cuda.synchronize()
+                kname = "k_score" if mode == "fp32" else "k_score_gemm"
+                ctx.reset_kernel_stats()
+                ctx.set_kernel_timing(True)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(args.steps):
+                    bioem.score(ctx, im, ps, cfg.max_shift, out=logp)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / args.steps
+                k_ms, k_n = ctx.kernel_time(kname)
+                launches += ctx.launch_count()
+                ctx.set_kernel_timing(False)
+                if ctx.status() != 0:
+                    raise RuntimeError(f"device status error ({name}, {mode})")
+                evals = n_img * n_ps
+                f = {"evals_per_s": evals / (ms / 1e3), "ms_per_step": ms, "kernel": kname,
+                     "kernel_ms_per_step": k_ms / args.steps, "launches_per_step": k_n / args.steps,
+                     "first_call_s": first_s}
+                if mode != "fp32":
+                    # dense contraction per launch: 3 products (hi hi, hi lo, lo hi) x 2 flop x K per
+                    # (parameter set, image, displacement), K = 2 N (N/2 + 1) real terms
+                    K = cfg.npix * (cfg.npix + 2)
+                    alg = 6.0 * K * evals * cfg.n_shift
+                    ipt = 256 // cfg.n_shift
+                    executed = 6.0 * K * (-(-n_ps // 128) * 128) * (-(-n_img // ipt) * 256)
+                    per_launch_ms = k_ms / max(1, k_n)
+                    achieved = alg / max(1, k_n / args.steps) / (per_launch_ms / 1e3) / 1e12
+                    f["roofline"] = {"bound": "tensor", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+                                     "frac": achieved / peak_tf, "traffic": None,
+                                     "peak_basis": "measured cuBLAS bf16 burst (FP16 has the same dense rate)",
+                                     "executed_tflops_incl_padding": executed / max(1, k_n / args.steps)
+                                     / (per_launch_ms / 1e3) / 1e12}
+                    f["operand_build_s"] = max(0.0, first_s - ms / 1e3)
+                forms[mode] = f
+            ctx.set_precision("fp32")
+            sizes[str(cfg.npix)] = {"config": workload_config(cfg, n_img, n_ps), "forms": forms}
+            im.close()
+            ps.close()
+    head = sizes["128"]["forms"]["fp16x2"]
+    line = {"metric": METRIC, "value": head["evals_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f16x2 (split FP16 operands, FP32 accumulation)", "data": "synthetic",
+            "config": {"workload": "precision: 64 images x 6912 parameter sets, shifts +-4, at 128 px and 64 px; "
+                                   "value = the FP16 two-term form at 128 px",
+                       "step": "bioem_score over resident images and projections"},
+            "roofline": head["roofline"], "sizes": sizes, "gpu_launches": int(launches), "clocks": clocks.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.workload == "proposal":
@@ -528,6 +627,8 @@ def main():
         return bench_reference(args)
     if args.workload == "batched":
         return bench_batched(args)
+    if args.workload == "precision":
+        return bench_precision(args)
     return bench_ours(args)
 
 

@@ -10,7 +10,7 @@
  *     Host pointers are named without the prefix.
  *   - Images are float32, row-major [n][ny][nx] (x fastest); pixel (j, k) is at
  *     x_j = (j - nx/2) * pixel_A, y_k = (k - ny/2) * pixel_A (Eq. 1's pixel positions).
- *     Only square images with nx = ny in {32, 64, 128} are supported in this version.
+ *     Only square images with nx = ny in {32, 64, 96, 128, 192} are supported in this version.
  *   - Handles (bioem_ctx, bioem_images, bioem_projset) are owned by the library and freed by
  *     the matching bioem_free_* / bioem_destroy call.
  *   - Work is enqueued asynchronously on the context's CUDA stream (the caller's stream; not
@@ -66,6 +66,25 @@ int bioem_set_stream(bioem_ctx* ctx, void* cuda_stream);
  * are processed in waves that fit.  Default 2 GiB. */
 int bioem_set_scratch_limit(bioem_ctx* ctx, unsigned long long bytes);
 
+/* Arithmetic of the correlation step (Sec. 3.9, single versus double precision; the paper's
+ * kernels are FP32).  BIOEM_PRECISION_FP32 (default): FP32 Fourier product and pruned inverse
+ * FFT on the CUDA cores.  BIOEM_PRECISION_BF16X2 / BIOEM_PRECISION_FP16X2: the inverse transform
+ * restricted to the displacement window written as one dense real matrix product on the tensor
+ * cores, every operand split into two 16-bit floats (hi + lo; FP16 with power-of-two scaling),
+ * products hi*hi + hi*lo + lo*hi accumulated in FP32; moments and log-sum-exps stay FP64.  The
+ * tensor forms need (2 max_shift + 1)^2 <= 256 and build, on first use, operand copies kept with
+ * the handles (freed with them): ceil(n_ps / 128) * 128 * nx * (nx + 2) * 4 bytes for a projection
+ * set and ceil(n_img / IPT) * 256 * nx * (nx + 2) * 4 bytes for images, IPT = floor(256 /
+ * (2 max_shift + 1)^2) images per 256-column tile.
+ * The mode applies to bioem_score, bioem_score_all, bioem_best_params and bioem_score_pairs;
+ * bioem_score_noalloc, the batched and the gathered entry points always use FP32.
+ * Errors: INVALID_ARG for an unknown mode. */
+#define BIOEM_PRECISION_FP32 0
+#define BIOEM_PRECISION_BF16X2 1
+#define BIOEM_PRECISION_FP16X2 2
+int bioem_set_precision(bioem_ctx* ctx, int mode);
+int bioem_get_precision(const bioem_ctx* ctx);
+
 /* Free the context and everything it owns (not the handles made with it). */
 void bioem_destroy(bioem_ctx* ctx);
 
@@ -114,7 +133,8 @@ int bioem_project_model(bioem_ctx* ctx, const float* d_atoms, int n_atoms, doubl
  *   d_logP_per_orient [n_img][nq] float64 device or NULL: ln of the mean over (ctf, d) of L for
  *                     each orientation (Sec. 3.8, posterior as a function of orientation).
  * Requires images and projset with the same nx, ny, pixel_A; 0 <= max_shift < nx/2 and
- * max_shift <= 16 (nx = 128), 8 (nx = 64), 4 (nx = 32).
+ * max_shift <= 4 (nx = 32), 8 (64), 12 (96), 16 (128), 24 (192) in the FP32 form, and
+ * (2 max_shift + 1)^2 <= 256 (max_shift <= 7) in the split-precision forms (bioem_set_precision).
  * Errors: INVALID_ARG, UNSUPPORTED_SIZE, OOM, CUDA; NUMERIC via the status word. */
 int bioem_score(bioem_ctx* ctx, const bioem_images* images, const bioem_projset* projset,
                 int max_shift, double* d_logP, double* d_logP_per_orient);

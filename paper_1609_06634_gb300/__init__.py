@@ -81,6 +81,20 @@ class Context:
     def set_scratch_limit(self, nbytes: int):
         _check(self, lib().bioem_set_scratch_limit(self._h, int(nbytes)), "set_scratch_limit")
 
+    PRECISIONS = {"fp32": 0, "bf16x2": 1, "fp16x2": 2}
+
+    def set_precision(self, mode):
+        """Arithmetic of the correlation step for score/score_all/best_params/score_pairs: "fp32"
+        (FFT form on the CUDA cores), "bf16x2" or "fp16x2" (two-term split-precision GEMM on the
+        tensor cores), or the C constant."""
+        m = self.PRECISIONS[mode] if isinstance(mode, str) else int(mode)
+        _check(self, lib().bioem_set_precision(self._h, m), "set_precision")
+
+    @property
+    def precision(self) -> str:
+        m = int(lib().bioem_get_precision(self._h))
+        return {v: k for k, v in self.PRECISIONS.items()}[m]
+
     def set_kernel_timing(self, on: bool = True):
         """Record CUDA events on this context's stream around every library kernel launch."""
         _check(self, lib().bioem_set_kernel_timing(self._h, 1 if on else 0), "set_kernel_timing")

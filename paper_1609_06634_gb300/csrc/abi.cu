@@ -27,7 +27,7 @@ int bioem_check_cuda(bioem_ctx* ctx, cudaError_t e, const char* what) {
 
 const char* const bioem_kernel_names[KID_COUNT] = {
     "k_prepare_images", "k_project", "k_ctf_table", "k_psf_spectra", "k_psf_real",
-    "k_score", "k_reduce_wave", "k_finalize", "k_pairs_out"};
+    "k_score", "k_reduce_wave", "k_finalize", "k_pairs_out", "k_gemm_ops", "k_score_gemm"};
 
 void bioem_launch_begin(bioem_ctx* ctx, int kid) {
     if (!ctx->timing) return;
@@ -194,6 +194,16 @@ void bioem_destroy(bioem_ctx* ctx) {
     delete ctx;
 }
 
+int bioem_set_precision(bioem_ctx* ctx, int mode) {
+    if (!ctx) return BIOEM_ERR_INVALID_ARG;
+    if (mode != BIOEM_PRECISION_FP32 && mode != BIOEM_PRECISION_BF16X2 && mode != BIOEM_PRECISION_FP16X2)
+        return bioem_set_error(ctx, BIOEM_ERR_INVALID_ARG, "unknown precision mode %d", mode);
+    ctx->precision = mode;
+    return BIOEM_OK;
+}
+
+int bioem_get_precision(const bioem_ctx* ctx) { return ctx ? ctx->precision : BIOEM_ERR_INVALID_ARG; }
+
 int bioem_set_kernel_timing(bioem_ctx* ctx, int enable) {
     if (!ctx) return BIOEM_ERR_INVALID_ARG;
     ctx->timing = enable ? 1 : 0;
@@ -235,7 +245,9 @@ int bioem_get_status(bioem_ctx* ctx, int* out_status) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream);
     if (e != cudaSuccess) return bioem_check_cuda(ctx, e, "status read");
-    *out_status = (h & BIOEM_DEV_NUMERIC) ? BIOEM_ERR_NUMERIC : (h ? BIOEM_ERR_CUDA : BIOEM_OK);
+    *out_status = (h & BIOEM_DEV_TIMEOUT)   ? BIOEM_ERR_TIMEOUT
+                  : (h & BIOEM_DEV_NUMERIC) ? BIOEM_ERR_NUMERIC
+                  : (h ? BIOEM_ERR_CUDA : BIOEM_OK);
     return BIOEM_OK;
 }
 
@@ -316,7 +328,8 @@ static int check_pair(bioem_ctx* ctx, const bioem_images* im, const bioem_projse
     if (im->nx != ps->nx || im->ny != ps->ny || fabs(im->pixel_A - ps->pixel_A) > 1e-9 * im->pixel_A)
         return bioem_set_error(ctx, BIOEM_ERR_INVALID_ARG, "images and projections differ in size or pixel");
     if (max_shift < 0) return bioem_set_error(ctx, BIOEM_ERR_INVALID_ARG, "negative max_shift");
-    if (!bioem_score_supported(im->nx, max_shift))
+    if (ctx->precision == BIOEM_PRECISION_FP32 ? !bioem_score_supported(im->nx, max_shift)
+                                               : !bioem_gemm_supported(im->nx, max_shift))
         return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE, "max_shift %d unsupported at %d px", max_shift, im->nx);
     if (ps->n_ps == 0) return bioem_set_error(ctx, BIOEM_ERR_INVALID_ARG, "empty parameter set");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return bioem_set_error(ctx, BIOEM_ERR_CUDA, "cudaSetDevice");
@@ -395,6 +408,7 @@ void bioem_free_images(bioem_images* im) {
     release(im->stream, im->d_spec);
     release(im->stream, im->d_kA);
     release(im->stream, im->d_amax);
+    bioem_gemm_cache_free(&im->gemm, im->stream);
     free(im);
 }
 
@@ -404,6 +418,7 @@ void bioem_free_projset(bioem_projset* ps) {
     release(ps->stream, ps->d_spec);
     release(ps->stream, ps->d_kB);
     release(ps->stream, ps->d_amax);
+    bioem_gemm_cache_free(&ps->gemm, ps->stream);
     free(ps);
 }
 

@@ -11,7 +11,7 @@
 // ------------------------------------------------------------------ kernel accounting
 enum bioem_kernel_id {
     KID_PREPARE = 0, KID_PROJECT, KID_CTF_TABLE, KID_PSF_SPECTRA, KID_PSF_REAL, KID_SCORE, KID_REDUCE_WAVE,
-    KID_FINALIZE, KID_PAIRS_OUT, KID_COUNT
+    KID_FINALIZE, KID_PAIRS_OUT, KID_GEMM_OPS, KID_SCORE_GEMM, KID_COUNT
 };
 extern const char* const bioem_kernel_names[KID_COUNT];
 
@@ -42,6 +42,17 @@ struct bioem_ctx {
     int timing;
     std::vector<bioem_timed_launch> pending;
     double kid_ms[KID_COUNT];
+    int precision;   // BIOEM_PRECISION_*: the form bioem_score and its relatives use
+};
+
+// Operands of the split-precision GEMM scoring form, built from a handle's spectra on first use
+// and kept with the handle (rebuilt when the precision or, for images, the shift window changes).
+struct bioem_gemm_cache {
+    void* d_ops;     // tile-ready hi/lo operand blocks
+    size_t bytes;
+    float* d_inv;    // per row (parameter set) or per image: 1 / power-of-two scale
+    int mode;        // BIOEM_PRECISION_* it was built for (0: none)
+    int shift;       // images: the displacement half-width of its columns
 };
 
 struct bioem_images {
@@ -53,6 +64,7 @@ struct bioem_images {
     float2* d_spec;   // [n_img][ny][nx/2 + 1] unit-norm half spectrum, DC = 0
     double* d_kA;     // [n_img] (3-n)/2 ln A + c(n)
     float* d_amax;    // [n_img] largest |coefficient| of the stored spectrum
+    mutable bioem_gemm_cache gemm;
 };
 
 struct bioem_projset {
@@ -64,10 +76,12 @@ struct bioem_projset {
     float2* d_spec;   // [n_ps][ny][nx/2 + 1] unit-norm PSF-filtered projection spectrum, DC = 0
     double* d_kB;     // [n_ps] -1/2 ln B
     float* d_amax;    // [n_ps] largest |coefficient| of the stored spectrum
+    mutable bioem_gemm_cache gemm;
 };
 
 // ------------------------------------------------------------------ status codes inside kernels
 #define BIOEM_DEV_NUMERIC 1
+#define BIOEM_DEV_TIMEOUT 2
 
 // ------------------------------------------------------------------ helpers
 __host__ __device__ inline int bioem_size_index(int n) {
@@ -120,6 +134,14 @@ int bioem_score_supported(int npix, int max_shift);
 int bioem_launch_score(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, int max_shift,
                        const bioem_score_out& out);
 int bioem_upload_score_twiddles(bioem_ctx* ctx);
+
+// gemm.cu (split-precision tensor-core form)
+int bioem_gemm_supported(int npix, int max_shift);
+int bioem_gemm_row_tile();
+int bioem_gemm_prepare(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, int max_shift, int mode);
+int bioem_gemm_records(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, int max_shift, int mode,
+                       int ps_lo, int ps_hi, float* rec_t, float* rec_s, int* rec_d);
+void bioem_gemm_cache_free(bioem_gemm_cache* c, cudaStream_t stream);
 
 // abi.cu
 void bioem_launch_begin(bioem_ctx* ctx, int kid);   // call before a kernel launch

@@ -517,23 +517,32 @@ __global__ void k_pairs_out(const float* __restrict__ rec_t, const float* __rest
 }
 
 // ---------------------------------------------------------------------------- host side
-template <class C>
-int run_score(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, int max_shift,
-              const bioem_score_out& out) {
+// The wave loop shared by the scoring forms: parameter sets [range) in waves whose per-pair records
+// (n_img x wave) fit the scratch limit; `records(wbegin, wl, rec_t, rec_s, rec_d)` enqueues the
+// kernel(s) writing the records of sets [wbegin, wbegin + wl), then the float64 reductions fold
+// them.  Records name displacements d = (dy + smax) ns + (dx + smax), ns = 2 smax + 1 (smax: the
+// record kernel's window, which may exceed the scored max_shift); the posterior is normalised by the
+// S = (2 max_shift + 1)^2 scored displacements.  Waves are multiples of `align` parameter sets (whole
+// orientations when per-orientation output is wanted).
+template <class Records>
+int run_waves(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, int max_shift, int smax, int align,
+              const bioem_score_out& out, Records&& records) {
     const int n_img = im->n_img;
-    const int n = C::N * C::N;
-    const int nsk = C::NS;
+    const int n = im->nx * im->ny;
+    const int nsk = 2 * smax + 1;
     const bool pairs_mode = out.pair_max != nullptr;
     const int range_begin = pairs_mode ? out.ps_begin : 0;
     const int range_len = pairs_mode ? out.ps_count : ps->n_ps;
     const int nctf = ps->nctf;
     if (n_img == 0 || range_len == 0) return BIOEM_OK;
 
-    // wave length: records of n_img x wave must fit the scratch limit; aligned to whole orientations
+    // wave length: records of n_img x wave must fit the scratch limit; a multiple of `align`
     const unsigned long long per_ps = (unsigned long long)n_img * 12ull;
     long long wave = (long long)(ctx->scratch_limit / per_ps);
+    if (wave >= align) wave -= wave % align;
+    const long long min_wave = pairs_mode ? 1 : nctf;
+    if (wave < min_wave) wave = min_wave;
     if (!pairs_mode) wave -= wave % nctf;
-    if (wave < (pairs_mode ? 1 : nctf)) wave = pairs_mode ? 1 : nctf;
     if (wave > range_len) wave = range_len;
     const size_t rec_need = (size_t)n_img * (size_t)wave * 12;
     if (ctx->rec_bytes < rec_need) {
@@ -556,39 +565,13 @@ int run_score(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, i
     float* rec_t = reinterpret_cast<float*>(ctx->d_rec);
     float* rec_s = rec_t + (size_t)n_img * wave;
     int* rec_d = reinterpret_cast<int*>(rec_s + (size_t)n_img * wave);
-
-    const size_t smem = C::SMEM;
-    if (cudaFuncSetAttribute(k_score<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return bioem_set_error(ctx, BIOEM_ERR_CUDA, "shared memory attribute (%zu bytes)", smem);
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score<C>, C::THREADS, smem) != cudaSuccess || per_sm < 1)
-        return bioem_set_error(ctx, BIOEM_ERR_CUDA, "occupancy query");
-    const int slots = per_sm * ctx->num_sms;
-    const float c1f = 0.5f * (3.0f - (float)n);
     const double c1 = 0.5 * (3.0 - (double)n);
     const int S = (2 * max_shift + 1) * (2 * max_shift + 1);
 
     for (long long w0 = 0; w0 < range_len; w0 += wave) {
         const int wl = (int)(range_len - w0 < wave ? range_len - w0 : wave);
         const int wbegin = range_begin + (int)w0;
-        // chunk: enough work items to keep every slot busy, at most 512 parameter sets
-        const long long target_items = 4ll * slots;
-        long long per_img = (target_items + n_img - 1) / n_img;
-        long long chunk = (wl + per_img - 1) / per_img;
-        chunk = ((chunk + C::PB - 1) / C::PB) * C::PB;
-        if (chunk > 512) chunk = 512;
-        if (chunk < C::PB) chunk = C::PB;
-        const long long n_chunks = (wl + chunk - 1) / chunk;
-        const long long n_items = n_chunks * n_img;
-        if (n_items > 0x7fffffffll) return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE, "too many work items");
-        const int grid = (int)(n_items < slots ? n_items : slots);
-        bioem_launch_begin(ctx, KID_SCORE);
-        k_score<C><<<grid, C::THREADS, smem, ctx->stream>>>(bioem_twiddles(ctx, C::N), im->d_spec, n_img, ps->d_spec,
-                                                             wbegin, wl, (int)chunk,
-                                                             (int)n_items, max_shift, c1f, rec_t, rec_s, rec_d,
-                                                             ctx->d_status);
-        bioem_launch_end(ctx, KID_SCORE);
-        int rc = bioem_check_cuda(ctx, cudaGetLastError(), "k_score");
+        int rc = records(wbegin, wl, rec_t, rec_s, rec_d);
         if (rc) return rc;
         if (pairs_mode) {
             bioem_launch_begin(ctx, KID_PAIRS_OUT);
@@ -611,12 +594,64 @@ int run_score(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, i
         const double log_norm = log((double)ps->n_ps * S);
         bioem_launch_begin(ctx, KID_FINALIZE);
         k_finalize<<<(n_img + 255) / 256, 256, 0, ctx->stream>>>(reinterpret_cast<const Acc*>(ctx->d_acc), n_img, log_norm,
-                                                                  nctf, nsk, C::SMAX, out.logP, out.best_q, out.best_ctf,
+                                                                  nctf, nsk, smax, out.logP, out.best_q, out.best_ctf,
                                                                   out.best_dx, out.best_dy, out.best_logL);
         bioem_launch_end(ctx, KID_FINALIZE);
         return bioem_check_cuda(ctx, cudaGetLastError(), "k_finalize");
     }
     return BIOEM_OK;
+}
+
+// The FP32 form: k_score<C> writes the records (displacements named in C's compile-time window).
+template <class C>
+int run_score(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, int max_shift,
+              const bioem_score_out& out) {
+    const int n_img = im->n_img;
+    const size_t smem = C::SMEM;
+    if (cudaFuncSetAttribute(k_score<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return bioem_set_error(ctx, BIOEM_ERR_CUDA, "shared memory attribute (%zu bytes)", smem);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score<C>, C::THREADS, smem) != cudaSuccess || per_sm < 1)
+        return bioem_set_error(ctx, BIOEM_ERR_CUDA, "occupancy query");
+    const int slots = per_sm * ctx->num_sms;
+    const float c1f = 0.5f * (3.0f - (float)(C::N * C::N));
+    auto records = [&](int wbegin, int wl, float* rec_t, float* rec_s, int* rec_d) -> int {
+        // chunk: enough work items to keep every slot busy, at most 512 parameter sets
+        const long long target_items = 4ll * slots;
+        long long per_img = (target_items + n_img - 1) / n_img;
+        long long chunk = (wl + per_img - 1) / per_img;
+        chunk = ((chunk + C::PB - 1) / C::PB) * C::PB;
+        if (chunk > 512) chunk = 512;
+        if (chunk < C::PB) chunk = C::PB;
+        const long long n_chunks = (wl + chunk - 1) / chunk;
+        const long long n_items = n_chunks * n_img;
+        if (n_items > 0x7fffffffll) return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE, "too many work items");
+        const int grid = (int)(n_items < slots ? n_items : slots);
+        bioem_launch_begin(ctx, KID_SCORE);
+        k_score<C><<<grid, C::THREADS, smem, ctx->stream>>>(bioem_twiddles(ctx, C::N), im->d_spec, n_img, ps->d_spec,
+                                                             wbegin, wl, (int)chunk, (int)n_items, max_shift, c1f,
+                                                             rec_t, rec_s, rec_d, ctx->d_status);
+        bioem_launch_end(ctx, KID_SCORE);
+        return bioem_check_cuda(ctx, cudaGetLastError(), "k_score");
+    };
+    return run_waves(ctx, im, ps, max_shift, C::SMAX, ps->nctf, out, records);
+}
+
+// The split-precision tensor-core form (gemm.cu writes the records, window = max_shift); waves are
+// whole 128-set row tiles where the scratch allows.
+int run_score_gemm(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, int max_shift,
+                   const bioem_score_out& out) {
+    const int mode = ctx->precision;
+    int rc = bioem_gemm_prepare(ctx, im, ps, max_shift, mode);
+    if (rc) return rc;
+    const int tile = bioem_gemm_row_tile();
+    int a = tile, b = ps->nctf;
+    while (b) { const int t = a % b; a = b; b = t; }
+    const int align = tile / a * ps->nctf;   // lcm(row tile, PSFs per orientation)
+    auto records = [&](int wbegin, int wl, float* rec_t, float* rec_s, int* rec_d) -> int {
+        return bioem_gemm_records(ctx, im, ps, max_shift, mode, wbegin, wbegin + wl, rec_t, rec_s, rec_d);
+    };
+    return run_waves(ctx, im, ps, max_shift, max_shift, align, out, records);
 }
 
 // <N, SMAX, pairs per batch, threads>
@@ -644,6 +679,13 @@ int bioem_score_supported(int npix, int max_shift) {
 
 int bioem_launch_score(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, int max_shift,
                        const bioem_score_out& out) {
+    if (ctx->precision != BIOEM_PRECISION_FP32) {
+        if (!bioem_gemm_supported(im->nx, max_shift))
+            return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE,
+                                   "split-precision form: max_shift %d at %d px exceeds 256 columns per image", max_shift,
+                                   im->nx);
+        return run_score_gemm(ctx, im, ps, max_shift, out);
+    }
     switch (im->nx) {
         case 32: return run_score<C32_4>(ctx, im, ps, max_shift, out);
         case 64: return max_shift <= 4 ? run_score<C64_4>(ctx, im, ps, max_shift, out)
