@@ -22,14 +22,18 @@
 // reductions that follow are shared.
 //
 // Kernel layout (one CTA per SM, persistent over 128 x 256 tiles): warp 0 streams operand chunks
-// with bulk asynchronous copies into a two-stage shared-memory ring, warp 1 allocates 512 tensor-
-// memory columns (two 256-column accumulators) and issues the MMAs from one thread, warps 2-5 read
-// an accumulator back (tcgen05.ld) while the next tile accumulates into the other.  Every wait on a
-// barrier is bounded in time; on expiry the kernel sets a status bit and leaves cleanly.
+// with bulk asynchronous copies into a four-stage shared-memory ring, warp 1 allocates 512 tensor-
+// memory columns (two 256-column accumulators) and issues the MMAs from one thread, warps 2-9 drain
+// an accumulator into FP32 registers (tcgen05.ld, then round-to-nearest adds) while the next group
+// of K chunks accumulates into the other.  The tensor cores' own FP32 accumulation, run over the
+// whole K of a tile, biased |rho| low by about 1e-5 (log P by -7e-3 at 128 px; one-signed, the
+// same for BF16 and FP16 operands); restarting it every GROUP chunks (48 MMAs) and summing the
+// partial products in registers removes most of that.  Every wait on a barrier is bounded in
+// time; on expiry the kernel sets a status bit and leaves cleanly.
 //
 // Operands are stored in global memory already in the tensor cores' shared-memory layout (K-major,
-// no swizzle: 8-row x 16-byte core matrices, the 8 core matrices of a 64-element K chunk 128 B
-// apart, 8-row groups 1024 B apart), one contiguous block per (tile, K chunk), hi block then lo
+// no swizzle: 8-row x 16-byte core matrices, the 4 core matrices of a 32-element K chunk 128 B
+// apart, 8-row groups 512 B apart), one contiguous block per (tile, K chunk), hi block then lo
 // block, so one bulk copy moves each.
 #include <math.h>
 #include <stdio.h>
@@ -43,15 +47,16 @@ namespace {
 
 constexpr int GM = 128;                        // parameter sets per tile (tensor-memory lanes)
 constexpr int GN = 256;                        // image-displacement columns per tile
-constexpr int KC = 64;                         // K elements per pipeline stage
+constexpr int KC = 32;                         // K elements per pipeline stage
 constexpr int KSTEP = 16;                      // K per MMA instruction (16-bit operands)
-constexpr int A_TERM = GM * KC * 2;            // bytes of one operand term of one stage: 16 KB
-constexpr int B_TERM = GN * KC * 2;            // 32 KB
-constexpr int STAGE = 2 * A_TERM + 2 * B_TERM; // 96 KB: A hi, A lo, B hi, B lo
-constexpr int NSTAGE = 2;
+constexpr int A_TERM = GM * KC * 2;            // bytes of one operand term of one stage: 8 KB
+constexpr int B_TERM = GN * KC * 2;            // 16 KB
+constexpr int RG_BYTES = KC * 16;              // one 8-row group: KC / 8 core matrices of 128 B
+constexpr int STAGE = 2 * A_TERM + 2 * B_TERM; // 48 KB: A hi, A lo, B hi, B lo
+constexpr int NSTAGE = 4;
 constexpr int EPI_THREADS = 256;               // epilogue: 8 warps, two per tensor-memory lane quarter
 constexpr int GEMM_THREADS = 64 + EPI_THREADS; // warp 0 copies, warp 1 MMAs, warps 2-9 epilogue
-constexpr int GROUP = 4;                       // K chunks accumulated in tensor memory before a drain
+constexpr int GROUP = 8;                       // K chunks accumulated in tensor memory before a drain (48 MMAs)
 constexpr size_t GEMM_SMEM = (size_t)NSTAGE * STAGE + 256;
 constexpr int TMEM_COLS = 2 * GN;
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per barrier wait
@@ -95,8 +100,8 @@ __global__ void k_gemm_ops_ps(const float2* __restrict__ spec, const float* __re
     const int lane = threadIdx.x & 31;
     const size_t nw = (size_t)gridDim.x * (blockDim.x >> 5);
     for (size_t cm = (size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); cm < total_cm; cm += nw) {
-        const int kg = (int)(cm & 7);
-        size_t rest = cm >> 3;
+        const int kg = (int)(cm % (KC / 8));
+        size_t rest = cm / (KC / 8);
         const int rg = (int)(rest % (GM / 8));
         rest /= (GM / 8);
         const int chunk = (int)(rest % n_chunks);
@@ -115,7 +120,7 @@ __global__ void k_gemm_ops_ps(const float2* __restrict__ spec, const float* __re
         uint32_t hi, lo;
         split2(v.x, v.y, fp16, hi, lo);
         unsigned char* blk = ops + (tile * n_chunks + chunk) * (size_t)(2 * A_TERM);
-        const int off = rg * 1024 + kg * 128 + lane * 4;
+        const int off = rg * RG_BYTES + kg * 128 + lane * 4;
         *reinterpret_cast<uint32_t*>(blk + off) = hi;
         *reinterpret_cast<uint32_t*>(blk + A_TERM + off) = lo;
     }
@@ -130,8 +135,8 @@ __global__ void k_gemm_ops_img(const float2* __restrict__ spec, const float* __r
     const int ns = 2 * smax + 1, ns2 = ns * ns;
     const size_t nw = (size_t)gridDim.x * (blockDim.x >> 5);
     for (size_t cm = (size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); cm < total_cm; cm += nw) {
-        const int kg = (int)(cm & 7);
-        size_t rest = cm >> 3;
+        const int kg = (int)(cm % (KC / 8));
+        size_t rest = cm / (KC / 8);
         const int rg = (int)(rest % (GN / 8));
         rest /= (GN / 8);
         const int chunk = (int)(rest % n_chunks);
@@ -163,7 +168,7 @@ __global__ void k_gemm_ops_img(const float2* __restrict__ spec, const float* __r
         uint32_t hi, lo;
         split2(gx, gy, fp16, hi, lo);
         unsigned char* blk = ops + (tile * n_chunks + chunk) * (size_t)(2 * B_TERM);
-        const int off = rg * 1024 + kg * 128 + lane * 4;
+        const int off = rg * RG_BYTES + kg * 128 + lane * 4;
         *reinterpret_cast<uint32_t*>(blk + off) = hi;
         *reinterpret_cast<uint32_t*>(blk + B_TERM + off) = lo;
     }
@@ -314,22 +319,20 @@ __device__ __forceinline__ Part part_merge(Part a, Part b, float c1) {
 }
 
 // One displacement's value into a running (t_min, sum, argmin): rho = v inv, t = log1p(-rho^2).
-__device__ __forceinline__ void part_add(Part& st, float v, float inv, int j, float c1, bool flag_numeric,
-                                         int* status) {
+// Branch-free (the lanes of a warp hold different parameter sets, so a data-dependent branch would
+// serialise both sides on every column), one exponential: e = exp(c1 |t - t_min|) either rescales
+// the sum to a new minimum (s e + 1) or is the new term (s + e).  r2max collects rho^2 for one
+// |rho| >= 1 check per tile.
+__device__ __forceinline__ void part_add(Part& st, float& r2max, float v, float inv, int j, float c1) {
     const float rho = v * inv;
-    float r2 = rho * rho;
-    if (r2 >= 1.0f) {
-        if (flag_numeric) atomicOr(status, BIOEM_DEV_NUMERIC);
-        r2 = 1.0f - 5.9604645e-8f;
-    }
-    const float tv = log1pf(-r2);
-    if (tv < st.t) {
-        st.s = st.s * __expf(c1 * (st.t - tv)) + 1.f;   // 0 * exp(-inf) = 0 on the first value
-        st.t = tv;
-        st.d = j;
-    } else {
-        st.s += __expf(c1 * (tv - st.t));
-    }
+    const float r2 = rho * rho;
+    r2max = fmaxf(r2max, r2);
+    const float tv = log1pf(-fminf(r2, 1.0f - 5.9604645e-8f));
+    const bool lower = tv < st.t;
+    const float e = __expf(c1 * fabsf(tv - st.t));   // the first value: exp(-inf) = 0, s = 0 * 0 + 1
+    st.s = lower ? fmaf(st.s, e, 1.f) : st.s + e;
+    st.d = lower ? j : st.d;
+    st.t = fminf(st.t, tv);
 }
 
 __device__ __forceinline__ bool warp_all(bool ok) { return __all_sync(0xffffffffu, ok) != 0; }
@@ -411,7 +414,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_score_gemm(const GemmArgs g
         }
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issue: each group of GROUP chunks into a fresh accumulator buffer
-        const uint32_t lbo = 128, sbo = 1024;
+        const uint32_t lbo = 128, sbo = RG_BYTES;
         uint32_t it = 0, gi = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
@@ -496,8 +499,23 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_score_gemm(const GemmArgs g
             int w = itile * g.ipt + ib;
             float inv = (ib < g.ipt && w < g.n_img) ? inv_p * __ldg(g.inv_img + w) : 0.f;
             Part st{INFINITY, 0.f, 0x7fffffff};
+            float r2max = 0.f;
+            // 8 blocks of 16 columns in a rolled loop (the likelihood body exists once in the code:
+            // unrolled over all 128 columns it crowded the instruction cache the MMA thread runs from)
+#pragma unroll 1
+            for (int blk = 0; blk < 8; ++blk) {
+                float v[16];
 #pragma unroll
-            for (int c = 0; c < 128; ++c) {
+                for (int k = 0; k < 16; ++k) v[k] = acc[k];
+#pragma unroll
+                for (int bb = 1; bb < 8; ++bb) {
+                    if (blk == bb) {
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) v[k] = acc[16 * bb + k];
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
                 if (j == ns2) {   // image ib complete
                     if (!fail && starts_here && ib < g.ipt && w < g.n_img && p_ok) {
                         const size_t o = (size_t)w * wl + (p - g.ps_lo);
@@ -514,9 +532,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_score_gemm(const GemmArgs g
                     inv = (ib < g.ipt && w < g.n_img) ? inv_p * __ldg(g.inv_img + w) : 0.f;
                     st = Part{INFINITY, 0.f, 0x7fffffff};
                 }
-                if (ib < g.ipt) part_add(st, acc[c], inv, j, g.c1, p_ok && w < g.n_img, g.status);
+                if (ib < g.ipt) part_add(st, r2max, v[k], inv, j, g.c1);
                 ++j;
+                }
             }
+            if (r2max >= 1.0f) atomicOr(g.status, BIOEM_DEV_NUMERIC);   // inv = 0 off the valid sets / images
             if (ib < g.ipt) {
                 if (h == 0 && cut) {
                     straddle[0][row] = st;   // first part of the cut image
@@ -599,7 +619,7 @@ int bioem_gemm_prepare(bioem_ctx* ctx, const bioem_images* im, const bioem_projs
         if (rc) return rc;
         if (cudaMemsetAsync(ps->gemm.d_inv, 0, sizeof(float) * n_ptiles * GM, ctx->stream) != cudaSuccess)
             return bioem_check_cuda(ctx, cudaGetLastError(), "operand scales");
-        const size_t total_cm = n_ptiles * n_chunks * (GM / 8) * 8;
+        const size_t total_cm = n_ptiles * n_chunks * (GM / 8) * (KC / 8);
         bioem_launch_begin(ctx, KID_GEMM_OPS);
         k_gemm_ops_ps<<<grid_for(ctx, total_cm), 256, 0, ctx->stream>>>(ps->d_spec, ps->d_amax, ps->n_ps, npix * nh,
                                                                        n_chunks, fp16, (unsigned char*)ps->gemm.d_ops,
@@ -621,7 +641,7 @@ int bioem_gemm_prepare(bioem_ctx* ctx, const bioem_images* im, const bioem_projs
         const size_t bytes = n_itiles * n_chunks * (size_t)(2 * B_TERM);
         int rc = alloc_cache(ctx, im->gemm, bytes, (size_t)im->n_img, "image operand");
         if (rc) return rc;
-        const size_t total_cm = n_itiles * n_chunks * (GN / 8) * 8;
+        const size_t total_cm = n_itiles * n_chunks * (GN / 8) * (KC / 8);
         bioem_launch_begin(ctx, KID_GEMM_OPS);
         k_gemm_ops_img<<<grid_for(ctx, total_cm), 256, 0, ctx->stream>>>(
             im->d_spec, im->d_amax, im->n_img, npix, nh, n_chunks, max_shift, ipt, fp16, bioem_twiddles(ctx, npix),
