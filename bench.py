@@ -432,6 +432,10 @@ def bench_batched(args):
     # which model explains each image best (images were drawn from seeded-random models)
     truth = np.concatenate([st["models"] for st in wl["stacks"]])
     acc = float(np.mean(np.argmax(out, axis=0) == truth))
+    # ensemble posterior of the 8 models over all images (Eq. 10), weights by EM
+    ens = bioem.ensemble(ctx, batch.out, n_iter=50)
+    ens_w = ens["weights"].cpu().numpy()
+    true_frac = np.bincount(truth, minlength=n_models) / len(truth)
     line = {"metric": METRIC, "value": batch.evals * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -439,7 +443,14 @@ def bench_batched(args):
                                    "(64/96/128/192 px, 140.8 A field), Hopf level 2 x 2 defocus x 2 B per stack, "
                                    "shifts N/8; one graph replay (persistent scoring launch + reduction) per step",
                        "evals_per_step": batch.evals, "setup_s": t_setup, "autotune_s": t_tune, "chunks": chunks},
-            "model_recovery": acc, "clocks": clocks.summary()}
+            "model_recovery": acc,
+            "ensemble": {"log_post_uniform_weights": None, "log_post_em": float(ens["log_post"]),
+                         "em_weights": [round(float(x), 4) for x in ens_w],
+                         "true_model_fractions": [round(float(x), 4) for x in true_frac],
+                         "model_rank_by_log_post": [int(i) for i in
+                                                    np.argsort(-ens["model_log_post"].cpu().numpy())]},
+            "clocks": clocks.summary()}
+    line["ensemble"]["log_post_uniform_weights"] = float(bioem.ensemble(ctx, batch.out)["log_post"])
     print(json.dumps(line), flush=True)
     batch.close()
     return 0

@@ -226,6 +226,23 @@ int bioem_score_gathered(bioem_ctx* ctx, const bioem_images* images, const bioem
                          int first);
 int bioem_acc_logP(bioem_ctx* ctx, const double* d_acc, int n_img, double log_norm, double* d_logP);
 
+/* Posterior of a weighted ensemble of models given a set of images (Sec. 2, Eq. 10):
+ *   ln P(M | Omega) = sum_w ln sum_m w_m P_mw   (up to a constant shared by all weightings),
+ * from d_logP [n_models][n_img] = ln P_mw as bioem_score or the batched matrix gives it (device;
+ * float64 if elem_bytes == 8, float32 if 4).  d_weights [n_models] float64 device: weights w_m >= 0,
+ * normalised to sum 1 in place (all zero or negative: NUMERIC in the status word, uniform used).
+ * With n_iter > 0, n_iter expectation-maximisation steps
+ *   r_mw = w_m P_mw / sum_m' w_m' P_m'w,   w_m <- (1 / n_img) sum_w r_mw
+ * first replace d_weights by weights of higher ensemble posterior (the objective is concave in w;
+ * the paper poses the weighting problem without an optimiser: this iteration is the textbook one
+ * for weights of fixed mixture components).  Outputs, float64 device:
+ *   d_out[0]      ln P(M | Omega) at the final weights;
+ *   d_out[1 + m]  sum_w ln P_mw, the log posterior of model m alone (its rank among the models).
+ * Sums run in a fixed order (deterministic).  1 <= n_models <= 512, n_img >= 1.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+int bioem_ensemble(bioem_ctx* ctx, const void* d_logP, int elem_bytes, int n_models, int n_img, double* d_weights,
+                   int n_iter, double* d_out);
+
 /* Learned orientation / defocus proposal (no counterpart in the paper).  A convolutional network
  * on the image averaged over downsample x downsample pixels and standardised: six 3x3 convolutions
  * of `channels` channels (strides 1, 2, 1, 2, 1, 2; ReLU), then two linear heads: n_qbins coarse

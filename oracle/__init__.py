@@ -16,6 +16,10 @@ What it computes (paper section / equation in brackets):
   for every displacement as a direct real-space sum [Sec. 3.3, Eqs. 11-12], the
   likelihood of Eq. 8 with N, mu and lambda integrated out in closed form
   [Sec. 3, first paragraph], and the grid sum of Eq. 9 as a log-sum-exp.
+* ``ensemble``: the posterior of a weighted ensemble of models over a set of
+  images [Sec. 2, Eq. 10], per-model posteriors, and the weights that maximise
+  it (an expectation-maximisation fixed point: our reading).
+* ``cnn``: the proposal network (not in the paper) and its chain-rule gradient.
 
 Everything is float64 numpy; library primitives (matmul, erf, lgamma) serve as
 steps.  Where the paper is silent or garbled, the function that takes a
@@ -45,6 +49,7 @@ from .forward import (  # noqa: F401
     synthesize_image,
     synthesize_images,
 )
+from .ensemble import em_weights, log_posterior, model_log_posteriors  # noqa: F401
 from .likelihood import (  # noqa: F401
     closed_form_loglik,
     correlation_all_shifts,

@@ -410,6 +410,22 @@ def acc_logP(ctx: Context, acc, log_norm: float):
     return out
 
 
+def ensemble(ctx: Context, logP, weights=None, n_iter: int = 0) -> dict:
+    """Ensemble posterior of Eq. 10 from a [n_models, n_img] device tensor of ln P (float32 or
+    float64): {"log_post": ln P(M | Omega) at the final weights, "weights": [n_models] float64,
+    "model_log_post": [n_models] sum over images of ln P of each model alone}."""
+    torch = _torch()
+    t = _dev_tensor(logP, logP.dtype if logP.dtype in (torch.float32, torch.float64) else torch.float64,
+                    ctx.device, "logP", ndim=2)
+    M, n = t.shape
+    w = torch.full((M,), 1.0 / M, dtype=torch.float64, device=ctx.device) if weights is None else \
+        _dev_tensor(weights, torch.float64, ctx.device, "weights", ndim=1).clone()
+    out = torch.empty(M + 1, dtype=torch.float64, device=ctx.device)
+    _check(ctx, lib().bioem_ensemble(ctx._h, _ptr(t), t.element_size(), int(M), int(n), _ptr(w), int(n_iter),
+                                     _ptr(out)), "ensemble")
+    return {"log_post": out[0], "weights": w, "model_log_post": out[1:]}
+
+
 def synthetic_maps(ctx: Context, atoms, sigma_A: float, quats, ctfs, npix: int, pixel_A: float):
     """bioem_synthetic_maps: I1 for pairs (quats[i], ctfs[i]) as a [n, npix, npix] float32 device tensor."""
     torch = _torch()
