@@ -569,7 +569,7 @@ def bench_precision(args):
                                      wl["ctfs"], cfg.npix, cfg.pixel_A)
             logp = torch.empty(n_img, dtype=torch.float64, device=dev)
             forms = {}
-            for mode in ("fp32", "bf16x2", "fp16x2"):
+            for mode in ("fp32", "bf16x2", "fp16x2", "bf16x2_real", "fp16x2_real"):
                 ctx.set_precision(mode)
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
@@ -600,8 +600,8 @@ def bench_precision(args):
                      "first_call_s": first_s}
                 if mode != "fp32":
                     # dense contraction per launch: 3 products (hi hi, hi lo, lo hi) x 2 flop x K per
-                    # (parameter set, image, displacement), K = 2 N (N/2 + 1) real terms
-                    K = cfg.npix * (cfg.npix + 2)
+                    # (parameter set, image, displacement), K = 2 N (N/2 + 1) real terms (N^2 in real space)
+                    K = cfg.npix * cfg.npix if mode.endswith("_real") else cfg.npix * (cfg.npix + 2)
                     alg = 6.0 * K * evals * cfg.n_shift
                     ipt = 256 // cfg.n_shift
                     executed = 6.0 * K * (-(-n_ps // 128) * 128) * (-(-n_img // ipt) * 256)
@@ -630,6 +630,75 @@ def bench_precision(args):
     return 0
 
 
+def bench_shifts(args):
+    """Where one back-transformation beats one correlation per displacement (Sec. 3.3, Fig. shifts),
+    reproduced on synthetic data: evals/s of the FP32 pruned-FFT form and of the tensor-core forms
+    (Fourier and real-space operands, BF16 two-term) against the shift half-width s, on the
+    precision workloads (64 images x 6912 parameter sets at 128 px and 64 px)."""
+    import torch
+
+    import paper_1609_06634_gb300 as bioem
+    from paper_1609_06634_gb300 import build
+
+    build.build()
+    dev = torch.device("cuda", 0)
+    ctx = bioem.Context(0)
+    stream = torch.cuda.current_stream(dev)
+    sweep, crossover = {}, {}
+    with ClockSampler(None) as clocks:
+        for name in ("precision128", "precision64"):
+            cfg = workloads.get_config(name)
+            n_img = args.n_img or cfg.n_img
+            wl = workloads.workload(cfg, n_img=0)
+            quats_np = wl["quats"] if args.n_quat is None else wl["quats"][:args.n_quat]
+            n_ps = len(quats_np) * len(wl["ctfs"])
+            atoms_d = torch.from_numpy(wl["atoms"]).to(dev)
+            im = bioem.prepare_images(ctx, synth_images(bioem, ctx, cfg, atoms_d, 0, n_img), cfg.pixel_A)
+            ps = bioem.project_model(ctx, atoms_d, cfg.sigma_A, torch.from_numpy(np.ascontiguousarray(quats_np)).to(dev),
+                                     wl["ctfs"], cfg.npix, cfg.pixel_A)
+            logp = torch.empty(n_img, dtype=torch.float64, device=dev)
+            fp32_max = {64: 8, 128: 16}[cfg.npix]
+            res = {}
+            for mode, shifts in [("fp32", sorted(set(list(range(0, 8)) + [8, 12, 16]))),
+                                 ("bf16x2", list(range(0, 8))), ("bf16x2_real", list(range(0, 8)))]:
+                res[mode] = {}
+                ctx.set_precision(mode)
+                for sh in shifts:
+                    if mode == "fp32" and sh > fp32_max:
+                        continue
+                    for _ in range(max(1, args.warmup)):
+                        bioem.score(ctx, im, ps, sh, out=logp)
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    for _ in range(args.steps):
+                        bioem.score(ctx, im, ps, sh, out=logp)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms = e0.elapsed_time(e1) / args.steps
+                    res[mode][sh] = n_img * n_ps / (ms / 1e3)
+                if ctx.status() != 0:
+                    raise RuntimeError(f"device status error ({name}, {mode})")
+            ctx.set_precision("fp32")
+            # smallest s at which the FFT form is at least as fast as the per-displacement forms
+            cross = next((sh for sh in range(0, 8) if res["fp32"][sh] >= max(res["bf16x2"][sh],
+                                                                                res["bf16x2_real"][sh])), None)
+            sweep[str(cfg.npix)] = {m: {str(k): v for k, v in r.items()} for m, r in res.items()}
+            crossover[str(cfg.npix)] = cross if cross is not None else "beyond s = 7 (tensor-core forms faster)"
+            im.close()
+            ps.close()
+    head = sweep["128"]["bf16x2"]["4"]
+    line = {"metric": METRIC, "value": head, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (FFT form) / bf16x2 (tensor-core forms)", "data": "synthetic",
+            "config": {"workload": "shift-window sweep: 64 images x 6912 parameter sets at 128 px and 64 px, "
+                                   "s = 0..16; value = BF16 two-term form at 128 px, s = 4",
+                       "step": "bioem_score over resident images and projections"},
+            "sweep_evals_per_s": sweep, "fft_form_first_as_fast_at_s": crossover, "clocks": clocks.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.workload == "proposal":
@@ -640,6 +709,8 @@ def main():
         return bench_batched(args)
     if args.workload == "precision":
         return bench_precision(args)
+    if args.workload == "shifts":
+        return bench_shifts(args)
     return bench_ours(args)
 
 

@@ -75,13 +75,18 @@ int bioem_set_scratch_limit(bioem_ctx* ctx, unsigned long long bytes);
  * tensor forms need (2 max_shift + 1)^2 <= 256 and build, on first use, operand copies kept with
  * the handles (freed with them): ceil(n_ps / 128) * 128 * nx * (nx + 2) * 4 bytes for a projection
  * set and ceil(n_img / IPT) * 256 * nx * (nx + 2) * 4 bytes for images, IPT = floor(256 /
- * (2 max_shift + 1)^2) images per 256-column tile.
+ * (2 max_shift + 1)^2) images per 256-column tile (nx^2 in place of nx (nx + 2) in real space).
  * The mode applies to bioem_score, bioem_score_all, bioem_best_params and bioem_score_pairs;
  * bioem_score_noalloc, the batched and the gathered entry points always use FP32.
  * Errors: INVALID_ARG for an unknown mode. */
 #define BIOEM_PRECISION_FP32 0
 #define BIOEM_PRECISION_BF16X2 1
 #define BIOEM_PRECISION_FP16X2 2
+/* The same tensor-core product in real space (Sec. 3.3's real-space variant, one correlation per
+ * displacement): K = N^2 pixels of the zero-mean, unit-norm projection against the displaced
+ * zero-mean, unit-norm image, instead of the 2 N (N/2 + 1) half-spectrum terms. */
+#define BIOEM_PRECISION_BF16X2_REAL 3
+#define BIOEM_PRECISION_FP16X2_REAL 4
 int bioem_set_precision(bioem_ctx* ctx, int mode);
 int bioem_get_precision(const bioem_ctx* ctx);
 

@@ -81,12 +81,13 @@ class Context:
     def set_scratch_limit(self, nbytes: int):
         _check(self, lib().bioem_set_scratch_limit(self._h, int(nbytes)), "set_scratch_limit")
 
-    PRECISIONS = {"fp32": 0, "bf16x2": 1, "fp16x2": 2}
+    PRECISIONS = {"fp32": 0, "bf16x2": 1, "fp16x2": 2, "bf16x2_real": 3, "fp16x2_real": 4}
 
     def set_precision(self, mode):
         """Arithmetic of the correlation step for score/score_all/best_params/score_pairs: "fp32"
         (FFT form on the CUDA cores), "bf16x2" or "fp16x2" (two-term split-precision GEMM on the
-        tensor cores), or the C constant."""
+        tensor cores over the half spectrum), "bf16x2_real" / "fp16x2_real" (the same GEMM over
+        real-space pixels), or the C constant."""
         m = self.PRECISIONS[mode] if isinstance(mode, str) else int(mode)
         _check(self, lib().bioem_set_precision(self._h, m), "set_precision")
 

@@ -196,7 +196,7 @@ void bioem_destroy(bioem_ctx* ctx) {
 
 int bioem_set_precision(bioem_ctx* ctx, int mode) {
     if (!ctx) return BIOEM_ERR_INVALID_ARG;
-    if (mode != BIOEM_PRECISION_FP32 && mode != BIOEM_PRECISION_BF16X2 && mode != BIOEM_PRECISION_FP16X2)
+    if (mode < BIOEM_PRECISION_FP32 || mode > BIOEM_PRECISION_FP16X2_REAL)
         return bioem_set_error(ctx, BIOEM_ERR_INVALID_ARG, "unknown precision mode %d", mode);
     ctx->precision = mode;
     return BIOEM_OK;

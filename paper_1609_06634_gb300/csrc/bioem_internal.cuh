@@ -116,6 +116,8 @@ int bioem_launch_synthetic(bioem_ctx* ctx, const float* d_atoms, int n_atoms, do
                            const float* d_quats, const bioem_ctf* ctfs, int n, int npix,
                            double pixel_A, float* d_out);
 double bioem_log_norm_constant(int n);
+// zero-mean, unit-norm real-space images of `count` stored half spectra, and max |x| of each
+int bioem_launch_spec_to_real(bioem_ctx* ctx, const float2* spec, int count, int npix, float* out, float* amax);
 
 // score.cu
 struct bioem_score_out {

@@ -174,6 +174,56 @@ __global__ void k_gemm_ops_img(const float2* __restrict__ spec, const float* __r
     }
 }
 
+// B operand of the real-space form (Sec. 3.3's real-space variant: one correlation per
+// displacement): column n of image tile `tile` is displacement d of image w; the K pair c holds
+// pixels r = 2c, 2c + 1 (same row: N is even) of the displaced image o'(r - d), indices mod N.
+// img: [n_img][N][N] zero-mean unit-norm real-space images; amax: max |o'| per image.
+__global__ void k_gemm_ops_img_real(const float* __restrict__ img, const float* __restrict__ amax, int n_img,
+                                    int npix, int n_chunks, int smax, int ipt, int fp16,
+                                    unsigned char* __restrict__ ops, size_t total_cm) {
+    const int lane = threadIdx.x & 31;
+    const int ns = 2 * smax + 1, ns2 = ns * ns;
+    const size_t nw = (size_t)gridDim.x * (blockDim.x >> 5);
+    for (size_t cm = (size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); cm < total_cm; cm += nw) {
+        const int kg = (int)(cm % (KC / 8));
+        size_t rest = cm / (KC / 8);
+        const int rg = (int)(rest % (GN / 8));
+        rest /= (GN / 8);
+        const int chunk = (int)(rest % n_chunks);
+        const size_t tile = rest / n_chunks;
+        const int n = rg * 8 + (lane >> 2);
+        const int ib = n / ns2;
+        const int d = n - ib * ns2;
+        const long long w = (long long)tile * ipt + ib;
+        const int c = chunk * (KC / 2) + kg * 4 + (lane & 3);
+        float gx = 0.f, gy = 0.f;
+        if (ib < ipt && w < n_img) {
+            const int r0 = 2 * c;
+            const int y = r0 / npix, x0 = r0 - (r0 / npix) * npix;
+            const int dy = d / ns - smax, dx = d - (d / ns) * ns - smax;
+            int ys = (y - dy) % npix;
+            ys += ys < 0 ? npix : 0;
+            int xs = (x0 - dx) % npix;
+            xs += xs < 0 ? npix : 0;
+            const int xs1 = xs + 1 == npix ? 0 : xs + 1;
+            const float* row = img + ((size_t)w * npix + ys) * npix;
+            gx = __ldg(row + xs);
+            gy = __ldg(row + xs1);
+            if (fp16) {
+                const int es = scale_exp(__ldg(amax + w));
+                gx = ldexpf(gx, es);
+                gy = ldexpf(gy, es);
+            }
+        }
+        uint32_t hi, lo;
+        split2(gx, gy, fp16, hi, lo);
+        unsigned char* blk = ops + (tile * n_chunks + chunk) * (size_t)(2 * B_TERM);
+        const int off = rg * RG_BYTES + kg * 128 + lane * 4;
+        *reinterpret_cast<uint32_t*>(blk + off) = hi;
+        *reinterpret_cast<uint32_t*>(blk + B_TERM + off) = lo;
+    }
+}
+
 // 1 / (scale of parameter set p) and 1 / (scale of image w), exact powers of two.
 __global__ void k_gemm_inv_scales(const float* __restrict__ amax, int n, float bound_factor, int fp16,
                                   float* __restrict__ inv) {
@@ -570,7 +620,14 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_score_gemm(const GemmArgs g
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
-int n_chunks_for(int npix) { return npix * (npix / 2 + 1) * 2 / KC; }
+bool mode_fp16(int mode) { return mode == BIOEM_PRECISION_FP16X2 || mode == BIOEM_PRECISION_FP16X2_REAL; }
+bool mode_real(int mode) { return mode == BIOEM_PRECISION_BF16X2_REAL || mode == BIOEM_PRECISION_FP16X2_REAL; }
+
+// K / KC: Fourier form K = 2 N (N/2 + 1) (real and imaginary parts of the half spectrum); real-space
+// form K = N^2 pixels.
+int n_chunks_for(int npix, int mode) {
+    return mode_real(mode) ? npix * npix / KC : npix * (npix / 2 + 1) * 2 / KC;
+}
 
 void release_cache(bioem_gemm_cache& c, cudaStream_t stream) {
     if (c.d_ops) cudaFreeAsync(c.d_ops, stream);
@@ -603,15 +660,32 @@ void bioem_gemm_cache_free(bioem_gemm_cache* c, cudaStream_t stream) { release_c
 int bioem_gemm_supported(int npix, int max_shift) {
     if (max_shift < 0 || 2 * max_shift >= npix) return 0;
     if ((2 * max_shift + 1) * (2 * max_shift + 1) > GN) return 0;
-    return bioem_size_index(npix) >= 0 && (npix * (npix / 2 + 1) * 2) % KC == 0;
+    return bioem_size_index(npix) >= 0 && (npix * (npix / 2 + 1) * 2) % KC == 0 && (npix * npix) % KC == 0;
 }
 
 int bioem_gemm_row_tile() { return GM; }
 
+// Real-space zero-mean unit-norm arrays [count][N][N] and their max |x| for `count` spectra, in
+// one stream-ordered temporary (freed by the caller with cudaFreeAsync).
+static int real_space(bioem_ctx* ctx, const float2* spec, int count, int npix, float** out, float** amax) {
+    const size_t n = (size_t)count * npix * npix;
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, sizeof(float) * (n + (size_t)count + 64), ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return bioem_set_error(ctx, BIOEM_ERR_OOM, "real-space operand scratch (%zu floats)", n);
+    }
+    *out = (float*)p;
+    *amax = (float*)p + n;
+    const int rc = bioem_launch_spec_to_real(ctx, spec, count, npix, *out, *amax);
+    if (rc) cudaFreeAsync(p, ctx->stream);
+    return rc;
+}
+
 int bioem_gemm_prepare(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, int max_shift, int mode) {
     const int npix = im->nx, nh = npix / 2 + 1;
-    const int n_chunks = n_chunks_for(npix);
-    const int fp16 = mode == BIOEM_PRECISION_FP16X2 ? 1 : 0;
+    const int n_chunks = n_chunks_for(npix, mode);
+    const int fp16 = mode_fp16(mode) ? 1 : 0;
+    const bool real = mode_real(mode);
     if (ps->gemm.mode != mode || !ps->gemm.d_ops) {
         const size_t n_ptiles = ((size_t)ps->n_ps + GM - 1) / GM;
         const size_t bytes = n_ptiles * n_chunks * (size_t)(2 * A_TERM);
@@ -619,16 +693,28 @@ int bioem_gemm_prepare(bioem_ctx* ctx, const bioem_images* im, const bioem_projs
         if (rc) return rc;
         if (cudaMemsetAsync(ps->gemm.d_inv, 0, sizeof(float) * n_ptiles * GM, ctx->stream) != cudaSuccess)
             return bioem_check_cuda(ctx, cudaGetLastError(), "operand scales");
+        // the A operand reads pairs of values: spectrum coefficients (Fourier form) or pairs of
+        // adjacent pixels of the real-space projection (real-space form)
+        const float2* src = ps->d_spec;
+        const float* amax = ps->d_amax;
+        float* tmp = nullptr;
+        if (real) {
+            float* ra = nullptr;
+            rc = real_space(ctx, ps->d_spec, ps->n_ps, npix, &tmp, &ra);
+            if (rc) return rc;
+            src = reinterpret_cast<const float2*>(tmp);
+            amax = ra;
+        }
+        const int ncoef = real ? npix * npix / 2 : npix * nh;
         const size_t total_cm = n_ptiles * n_chunks * (GM / 8) * (KC / 8);
         bioem_launch_begin(ctx, KID_GEMM_OPS);
-        k_gemm_ops_ps<<<grid_for(ctx, total_cm), 256, 0, ctx->stream>>>(ps->d_spec, ps->d_amax, ps->n_ps, npix * nh,
-                                                                       n_chunks, fp16, (unsigned char*)ps->gemm.d_ops,
-                                                                       total_cm);
+        k_gemm_ops_ps<<<grid_for(ctx, total_cm), 256, 0, ctx->stream>>>(src, amax, ps->n_ps, ncoef, n_chunks, fp16,
+                                                                       (unsigned char*)ps->gemm.d_ops, total_cm);
         bioem_launch_end(ctx, KID_GEMM_OPS);
         bioem_launch_begin(ctx, KID_GEMM_OPS);
-        k_gemm_inv_scales<<<(ps->n_ps + 255) / 256, 256, 0, ctx->stream>>>(ps->d_amax, ps->n_ps, 1.f, fp16,
-                                                                           ps->gemm.d_inv);
+        k_gemm_inv_scales<<<(ps->n_ps + 255) / 256, 256, 0, ctx->stream>>>(amax, ps->n_ps, 1.f, fp16, ps->gemm.d_inv);
         bioem_launch_end(ctx, KID_GEMM_OPS);
+        if (tmp) cudaFreeAsync(tmp, ctx->stream);
         rc = bioem_check_cuda(ctx, cudaGetLastError(), "k_gemm_ops_ps");
         if (rc) return rc;
         ps->gemm.mode = mode;
@@ -642,15 +728,30 @@ int bioem_gemm_prepare(bioem_ctx* ctx, const bioem_images* im, const bioem_projs
         int rc = alloc_cache(ctx, im->gemm, bytes, (size_t)im->n_img, "image operand");
         if (rc) return rc;
         const size_t total_cm = n_itiles * n_chunks * (GN / 8) * (KC / 8);
-        bioem_launch_begin(ctx, KID_GEMM_OPS);
-        k_gemm_ops_img<<<grid_for(ctx, total_cm), 256, 0, ctx->stream>>>(
-            im->d_spec, im->d_amax, im->n_img, npix, nh, n_chunks, max_shift, ipt, fp16, bioem_twiddles(ctx, npix),
-            (unsigned char*)im->gemm.d_ops, total_cm);
-        bioem_launch_end(ctx, KID_GEMM_OPS);
-        bioem_launch_begin(ctx, KID_GEMM_OPS);
-        k_gemm_inv_scales<<<(im->n_img + 255) / 256, 256, 0, ctx->stream>>>(im->d_amax, im->n_img, 2.8285f, fp16,
-                                                                            im->gemm.d_inv);
-        bioem_launch_end(ctx, KID_GEMM_OPS);
+        if (real) {
+            float *tmp = nullptr, *ra = nullptr;
+            rc = real_space(ctx, im->d_spec, im->n_img, npix, &tmp, &ra);
+            if (rc) return rc;
+            bioem_launch_begin(ctx, KID_GEMM_OPS);
+            k_gemm_ops_img_real<<<grid_for(ctx, total_cm), 256, 0, ctx->stream>>>(
+                tmp, ra, im->n_img, npix, n_chunks, max_shift, ipt, fp16, (unsigned char*)im->gemm.d_ops, total_cm);
+            bioem_launch_end(ctx, KID_GEMM_OPS);
+            bioem_launch_begin(ctx, KID_GEMM_OPS);
+            k_gemm_inv_scales<<<(im->n_img + 255) / 256, 256, 0, ctx->stream>>>(ra, im->n_img, 1.f, fp16,
+                                                                                im->gemm.d_inv);
+            bioem_launch_end(ctx, KID_GEMM_OPS);
+            cudaFreeAsync(tmp, ctx->stream);
+        } else {
+            bioem_launch_begin(ctx, KID_GEMM_OPS);
+            k_gemm_ops_img<<<grid_for(ctx, total_cm), 256, 0, ctx->stream>>>(
+                im->d_spec, im->d_amax, im->n_img, npix, nh, n_chunks, max_shift, ipt, fp16,
+                bioem_twiddles(ctx, npix), (unsigned char*)im->gemm.d_ops, total_cm);
+            bioem_launch_end(ctx, KID_GEMM_OPS);
+            bioem_launch_begin(ctx, KID_GEMM_OPS);
+            k_gemm_inv_scales<<<(im->n_img + 255) / 256, 256, 0, ctx->stream>>>(im->d_amax, im->n_img, 2.8285f, fp16,
+                                                                                im->gemm.d_inv);
+            bioem_launch_end(ctx, KID_GEMM_OPS);
+        }
         rc = bioem_check_cuda(ctx, cudaGetLastError(), "k_gemm_ops_img");
         if (rc) return rc;
         im->gemm.mode = mode;
@@ -670,7 +771,7 @@ int bioem_gemm_records(bioem_ctx* ctx, const bioem_images* im, const bioem_projs
     g.b_ops = (const unsigned char*)im->gemm.d_ops;
     g.inv_ps = ps->gemm.d_inv;
     g.inv_img = im->gemm.d_inv;
-    g.n_chunks = n_chunks_for(npix);
+    g.n_chunks = n_chunks_for(npix, mode);
     g.ptile0 = ps_lo / GM;
     g.n_ptiles = (ps_hi + GM - 1) / GM - g.ptile0;
     g.ipt = GN / ns2;
@@ -681,7 +782,7 @@ int bioem_gemm_records(bioem_ctx* ctx, const bioem_images* im, const bioem_projs
     g.ps_hi = ps_hi;
     const int n = npix * npix;
     g.c1 = 0.5f * (3.0f - (float)n);
-    const uint32_t fmt = mode == BIOEM_PRECISION_FP16X2 ? 0u : 1u;   // 0 FP16, 1 BF16
+    const uint32_t fmt = mode_fp16(mode) ? 0u : 1u;   // 0 FP16, 1 BF16
     g.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(GN >> 3) << 17) | ((uint32_t)(GM >> 4) << 24);
     g.rec_t = rec_t;
     g.rec_s = rec_s;

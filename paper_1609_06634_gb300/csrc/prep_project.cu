@@ -422,6 +422,63 @@ __global__ void __launch_bounds__(kThreads) k_psf_real(const float* __restrict__
     }
 }
 
+// Real-space image of a stored unit-norm half spectrum S (Eq. 3, inverse transform):
+//   x(r) = Re sum_k w_kx S(k) exp(+2 pi i k.r / N),  w = 1 on kx = 0, N/2 and 2 elsewhere,
+// rescaled to unit norm (float64 sum of squares); zero-mean because S(0) = 0.  With the forward
+// transforms above this is the zero-mean, unit-norm image whose correlations the scoring kernels
+// evaluate: sum_r o'(r) c'(r + d) = rho(d).  Writes x [N][N] and max |x|.
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_spec_to_real(const float2* __restrict__ spec,
+                                                           const float2* __restrict__ g_tw, float* __restrict__ out,
+                                                           float* __restrict__ amax) {
+    constexpr int H = N / 2 + 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2* F = reinterpret_cast<float2*>(smem);
+    float2* tw = F + N * H;
+    double* red = reinterpret_cast<double*>(tw + N);
+    const int i = blockIdx.x;
+    load_twiddles<N>(g_tw, tw);
+    const float2* S = spec + (size_t)i * N * H;
+    for (int o = threadIdx.x; o < N * H; o += blockDim.x) F[o] = S[o];
+    __syncthreads();
+    c2c_columns_inplace<N, true>(F, tw);
+    float* xo = out + (size_t)i * N * N;
+    double e = 0.0, dummy = 0.0;
+    for (int p = threadIdx.x; p < N * N; p += blockDim.x) {
+        const int y = p / N, x = p - (p / N) * N;
+        const float2* G = F + y * H;
+        const float v = G[0].x + ((x & 1) ? -G[N / 2].x : G[N / 2].x);
+        float acc = 0.f;
+        int idx = x;
+        for (int kx = 1; kx < N / 2; ++kx) {
+            const float2 w = tw[idx];   // exp(-2 pi i kx x / N); conjugated below
+            acc = fmaf(G[kx].x, w.x, fmaf(G[kx].y, w.y, acc));
+            idx += x;
+            idx -= (idx >= N) ? N : 0;
+        }
+        const float r = v + 2.f * acc;
+        xo[p] = r;
+        e += (double)r * r;
+    }
+    block_sum2(e, dummy, red);
+    const float scale = e > 0.0 ? (float)(1.0 / sqrt(e)) : 0.f;
+    float mx = 0.f;
+    for (int p = threadIdx.x; p < N * N; p += blockDim.x) {   // the same elements this thread wrote
+        const float r = xo[p] * scale;
+        xo[p] = r;
+        mx = fmaxf(mx, fabsf(r));
+    }
+    float* redf = reinterpret_cast<float*>(red);
+    __syncthreads();
+    redf[threadIdx.x] = mx;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) redf[threadIdx.x] = fmaxf(redf[threadIdx.x], redf[threadIdx.x + st]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) amax[i] = redf[0];
+}
+
 template <int N>
 size_t fwd_smem() {
     return (size_t)(N * (N / 2 + 1) + N) * sizeof(float2) + 2 * kThreads * sizeof(double);
@@ -553,6 +610,16 @@ int launch_synthetic_n(bioem_ctx* ctx, const float* d_atoms, int n_atoms, double
     return rc;
 }
 
+template <int N>
+int launch_spec_to_real_n(bioem_ctx* ctx, const float2* spec, int count, float* out, float* amax) {
+    const size_t sm = fwd_smem<N>();
+    if (set_smem<N>((const void*)k_spec_to_real<N>, sm)) return bioem_set_error(ctx, BIOEM_ERR_CUDA, "smem attribute");
+    bioem_launch_begin(ctx, KID_GEMM_OPS);
+    k_spec_to_real<N><<<count, kThreads, sm, ctx->stream>>>(spec, bioem_twiddles(ctx, N), out, amax);
+    bioem_launch_end(ctx, KID_GEMM_OPS);
+    return bioem_check_cuda(ctx, cudaGetLastError(), "k_spec_to_real");
+}
+
 }  // namespace
 
 double bioem_log_norm_constant(int n) {
@@ -581,6 +648,13 @@ int bioem_launch_project(bioem_ctx* ctx, const float* d_atoms, int n_atoms, doub
                          int nq, const bioem_ctf* ctfs, int nctf, bioem_projset* ps) {
 #define CALL(N) launch_project_n<N>(ctx, d_atoms, n_atoms, sigma_A, d_quats, nq, ctfs, nctf, ps)
     BIOEM_DISPATCH_N(ps->nx, CALL)
+#undef CALL
+}
+
+int bioem_launch_spec_to_real(bioem_ctx* ctx, const float2* spec, int count, int npix, float* out, float* amax) {
+    if (count <= 0) return BIOEM_OK;
+#define CALL(N) launch_spec_to_real_n<N>(ctx, spec, count, out, amax)
+    BIOEM_DISPATCH_N(npix, CALL)
 #undef CALL
 }
 

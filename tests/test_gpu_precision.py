@@ -1,5 +1,6 @@
 """GPU parity of the split-precision tensor-core scoring forms (BF16 and FP16 two-term GEMMs, Sec. 3.9's
-single- versus double-precision question taken to 16-bit operands) against the FP64 oracle.
+single- versus double-precision question taken to 16-bit operands; over the half spectrum and, as in
+Sec. 3.3's real-space variant, over pixels) against the FP64 oracle.
 
 Tolerance: |d log P| <= 1e-2 per image for the split-precision forms (the FP32 form's bound stays
 1e-3, checked on the same inputs).  Maximising grid points must match wherever the oracle's best
@@ -17,7 +18,7 @@ import workloads
 pytestmark = pytest.mark.gpu
 TOL = 1e-2
 TOL_FP32 = 1e-3
-MODES = ["bf16x2", "fp16x2"]
+MODES = ["bf16x2", "fp16x2", "bf16x2_real", "fp16x2_real"]
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
@@ -153,7 +154,8 @@ def test_mode_switch_rebuilds_operands(bioem, ctx):
     first = _score(bioem, ctx, "fp32", im, ps, 4)["logP"]
     r4 = oracle.score(imgs, wl["atoms"], quats, wl["ctfs"], cfg.sigma_A, cfg.pixel_A, 4)["logP"]
     r2 = oracle.score(imgs, wl["atoms"], quats, wl["ctfs"], cfg.sigma_A, cfg.pixel_A, 2)["logP"]
-    for mode, s, ref in [("bf16x2", 4, r4), ("fp16x2", 4, r4), ("bf16x2", 2, r2), ("fp16x2", 2, r2)]:
+    for mode, s, ref in [("bf16x2", 4, r4), ("fp16x2", 4, r4), ("bf16x2", 2, r2), ("fp16x2_real", 2, r2),
+                         ("bf16x2_real", 4, r4), ("fp16x2", 2, r2)]:
         np.testing.assert_allclose(_score(bioem, ctx, mode, im, ps, s)["logP"], ref, rtol=0, atol=TOL)
     np.testing.assert_array_equal(_score(bioem, ctx, "fp32", im, ps, 4)["logP"], first)
 
