@@ -164,6 +164,18 @@ int bioem_score_pairs(bioem_ctx* ctx, const bioem_images* images, const bioem_pr
                       int max_shift, int ps_begin, int ps_count, double* d_pair_max,
                       double* d_pair_lse);
 
+/* One chunk of a chunked (resumable) scan: folds every parameter set of `projset` into running
+ * per-image accumulators d_acc [n_img][2] float64 device = (M, S) with ln sum_{p,d} L = M + ln S,
+ * the state of Eq. 9's sum over the parameter sets scored so far (first != 0 starts it).  A grid
+ * too large for device memory is projected and scored chunk by chunk (the paper splits the images
+ * instead, Sec. 4.3); the accumulators can be copied to the host between chunks (a checkpoint) and
+ * loaded again to resume, and accumulators of disjoint chunks merge with the same operator
+ * (M, S) + (M', S') = (m, S e^{M - m} + S' e^{M' - m}), m = max(M, M').  After the last chunk
+ * bioem_acc_logP with log_norm = ln(total parameter sets x S) gives what bioem_score gives.
+ * Uses the context's precision mode.  Errors as bioem_score. */
+int bioem_score_accumulate(bioem_ctx* ctx, const bioem_images* images, const bioem_projset* projset, int max_shift,
+                           double* d_acc, int first);
+
 /* Synthetic maps (Sec. 3.8): the PSF-filtered projection I1 = F^-1[F(I0) CTF Env] (Eq. 5) of
  * the model for n pairs (d_quats[i], ctfs[i]), written to d_out [n][ny][nx] float32 device.
  * Same model arguments as bioem_project_model; ctfs is a HOST array of n entries. */

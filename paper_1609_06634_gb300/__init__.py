@@ -411,6 +411,17 @@ def acc_logP(ctx: Context, acc, log_norm: float):
     return out
 
 
+def score_accumulate(ctx: Context, images: Images, projset: ProjSet, max_shift: int, acc, first: bool):
+    """Fold every parameter set of `projset` into acc [n_img, 2] float64 (max, sum) accumulators."""
+    torch = _torch()
+    a = _dev_tensor(acc, torch.float64, ctx.device, "acc", ndim=2, last=2)
+    if a.data_ptr() != acc.data_ptr():
+        raise BioEMError(ERR_INVALID_ARG, "acc must be contiguous")
+    _check(ctx, lib().bioem_score_accumulate(ctx._h, images._h, projset._h, int(max_shift), _ptr(acc), 1 if first else 0),
+           "score_accumulate")
+    return acc
+
+
 def ensemble(ctx: Context, logP, weights=None, n_iter: int = 0) -> dict:
     """Ensemble posterior of Eq. 10 from a [n_models, n_img] device tensor of ln P (float32 or
     float64): {"log_post": ln P(M | Omega) at the final weights, "weights": [n_models] float64,

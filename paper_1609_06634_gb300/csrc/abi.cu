@@ -386,6 +386,17 @@ int bioem_score_pairs(bioem_ctx* ctx, const bioem_images* images, const bioem_pr
     return bioem_launch_score(ctx, images, projset, max_shift, out);
 }
 
+int bioem_score_accumulate(bioem_ctx* ctx, const bioem_images* images, const bioem_projset* projset, int max_shift,
+                           double* d_acc, int first) {
+    int rc = check_pair(ctx, images, projset, max_shift);
+    if (rc) return rc;
+    if (images->n_img > 0 && !d_acc) return bioem_set_error(ctx, BIOEM_ERR_INVALID_ARG, "score_accumulate: d_acc");
+    bioem_score_out out{};
+    out.acc2 = d_acc;
+    out.acc_first = first ? 1 : 0;
+    return bioem_launch_score(ctx, images, projset, max_shift, out);
+}
+
 int bioem_synthetic_maps(bioem_ctx* ctx, const float* d_atoms, int n_atoms, double sigma_A, const float* d_quats,
                          const bioem_ctf* ctfs, int n, int nx, int ny, double pixel_A, float* d_out) {
     if (!ctx) return BIOEM_ERR_INVALID_ARG;

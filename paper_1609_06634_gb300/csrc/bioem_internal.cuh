@@ -131,6 +131,8 @@ struct bioem_score_out {
     double* pair_max;   // score_pairs mode
     double* pair_lse;
     int ps_begin, ps_count;
+    double* acc2;       // bioem_score_accumulate: caller's [n_img][2] (max, sum exp(. - max)) of ln L
+    int acc_first;      // overwrite acc2 instead of folding into it
 };
 int bioem_score_supported(int npix, int max_shift);
 int bioem_launch_score(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, int max_shift,

@@ -516,6 +516,24 @@ __global__ void k_pairs_out(const float* __restrict__ rec_t, const float* __rest
     }
 }
 
+// Fold this call's per-image (max, sum) into the caller's running pairs acc2[w] = (M, S), ln sum L =
+// M + ln S; first != 0 overwrites.
+__global__ void k_fold_acc(const Acc* __restrict__ acc, int n_img, double* __restrict__ acc2, int first) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= n_img) return;
+    double M = acc[w].M, S = acc[w].S;
+    if (!first) {
+        const double M0 = acc2[2 * w], S0 = acc2[2 * w + 1];
+        if (M0 > -INFINITY) {
+            if (!(M > -INFINITY)) { M = M0; S = S0; }
+            else if (M0 > M) { S = S * exp(M - M0) + S0; M = M0; }
+            else S += S0 * exp(M0 - M);
+        }
+    }
+    acc2[2 * w] = M;
+    acc2[2 * w + 1] = S;
+}
+
 // ---------------------------------------------------------------------------- host side
 // The wave loop shared by the scoring forms: parameter sets [range) in waves whose per-pair records
 // (n_img x wave) fit the scratch limit; `records(wbegin, wl, rec_t, rec_s, rec_d)` enqueues the
@@ -597,6 +615,12 @@ int run_waves(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, i
                                                                   nctf, nsk, smax, out.logP, out.best_q, out.best_ctf,
                                                                   out.best_dx, out.best_dy, out.best_logL);
         bioem_launch_end(ctx, KID_FINALIZE);
+        if (out.acc2) {
+            bioem_launch_begin(ctx, KID_FINALIZE);
+            k_fold_acc<<<(n_img + 255) / 256, 256, 0, ctx->stream>>>(reinterpret_cast<const Acc*>(ctx->d_acc), n_img,
+                                                                     out.acc2, out.acc_first);
+            bioem_launch_end(ctx, KID_FINALIZE);
+        }
         return bioem_check_cuda(ctx, cudaGetLastError(), "k_finalize");
     }
     return BIOEM_OK;
