@@ -69,6 +69,35 @@ def train(net: CNN, images, yq, yd, epochs: int, batch: int, lr: float, gen) -> 
     return losses
 
 
+def redraw_nuisance(d: dict, cfg, rng) -> dict:
+    """The same projections (model, orientation, defocus, B) with new displacements, normalisations
+    and offsets; compose() then adds new noise.  Training on a fresh draw every epoch keeps the
+    network from memorising the noise of a fixed set of training images."""
+    n = len(d["quat"])
+    s = cfg.max_shift
+    e = dict(d)
+    e["dx"] = rng.integers(-s, s + 1, n)
+    e["dy"] = rng.integers(-s, s + 1, n)
+    e["norm"] = rng.uniform(0.5, 2.0, n)
+    e["offset"] = rng.uniform(-1.0, 1.0, n)
+    return e
+
+
+def train_redrawn(ctx: Context, net: CNN, atoms_dev: list, d: dict, cfg, epochs: int, batch: int, lr: float, gen,
+                  rng, images=None) -> list:
+    """Adam epochs, each over the training projections composed with a fresh draw of displacement,
+    normalisation, offset and noise (the first epoch uses `images` if given)."""
+    torch = _torch()
+    yq = torch.from_numpy(d["label_q"]).to(ctx.device)
+    yd = torch.from_numpy(d["label_d"]).to(ctx.device)
+    losses = []
+    for ep in range(epochs):
+        if images is None or ep > 0:
+            images = compose(ctx, atoms_dev, redraw_nuisance(d, cfg, rng) if ep > 0 else d, cfg, gen, out=images)
+        losses += train(net, images, yq, yd, epochs=1, batch=batch, lr=lr, gen=gen)
+    return losses
+
+
 def score_cells(ctx: Context, images, atoms_dev, bins: np.ndarray, cfg, wave: int = 256) -> dict:
     """ln P of every image over the union of its joint cells bins[i] (coarse cell * n_defocus + defocus
     bin), each cell expanded to its fine orientations x the cell's defocus x every B.  ln P is

@@ -106,6 +106,22 @@ def test_ragged_tiles_and_windows(bioem, ctx, mode, name, nq, n_img, max_shift):
     _check_best(out, ref, TOL)
 
 
+@pytest.mark.parametrize("npix,max_shift", [(96, 5), (192, 7)])
+@pytest.mark.parametrize("mode", ["bf16x2", "fp16x2_real"])
+def test_other_image_sizes(bioem, ctx, mode, npix, max_shift):
+    """96 and 192 px (K = 9408 / 37,248 Fourier terms, 9216 / 36,864 pixels), ragged tiles."""
+    cfg = workloads.get_config("tiny", npix=npix, pixel_A=2.0)
+    wl = workloads.workload(cfg, n_img=3)
+    imgs = oracle.synthesize_images(wl)
+    quats = wl["quats"][:23]
+    ref = oracle.score(imgs, wl["atoms"], quats, wl["ctfs"], cfg.sigma_A, cfg.pixel_A, max_shift)
+    im, ps = _handles(bioem, ctx, imgs, wl["atoms"], quats, wl["ctfs"], cfg)
+    out = _score(bioem, ctx, mode, im, ps, max_shift, per_orient=True, best=True)
+    np.testing.assert_allclose(out["logP"], ref["logP"], rtol=0, atol=TOL)
+    np.testing.assert_allclose(out["logP_orient"], ref["logP_orient"], rtol=0, atol=TOL)
+    _check_best(out, ref, TOL)
+
+
 @pytest.mark.parametrize("mode", MODES)
 def test_pairs_unaligned_range(bioem, ctx, mode):
     """score_pairs over sets [100, 800): row tiles cut by the range at both ends."""
