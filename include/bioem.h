@@ -243,6 +243,13 @@ int bioem_score_gathered(bioem_ctx* ctx, const bioem_images* images, const bioem
                          int first);
 int bioem_acc_logP(bioem_ctx* ctx, const double* d_acc, int n_img, double log_norm, double* d_logP);
 
+/* Per-pair values of the same per-image lists (for re-ranking candidates): d_pair_lse [nnz] float64
+ * device, d_pair_lse[i] = ln sum_d L(w | d_ps_idx[i], d) for the image w whose list holds entry i.
+ * Arguments and errors as bioem_score_gathered. */
+int bioem_score_gathered_pairs(bioem_ctx* ctx, const bioem_images* images, const bioem_projset* projset, int max_shift,
+                               const int* d_offsets, const int* d_ps_idx, int nnz, int max_per_image,
+                               double* d_pair_lse);
+
 /* Posterior of a weighted ensemble of models given a set of images (Sec. 2, Eq. 10):
  *   ln P(M | Omega) = sum_w ln sum_m w_m P_mw   (up to a constant shared by all weightings),
  * from d_logP [n_models][n_img] = ln P_mw as bioem_score or the batched matrix gives it (device;

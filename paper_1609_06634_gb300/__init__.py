@@ -403,6 +403,18 @@ def score_gathered(ctx: Context, images: Images, projset: ProjSet, max_shift: in
     return acc
 
 
+def score_gathered_pairs(ctx: Context, images: Images, projset: ProjSet, max_shift: int, offsets, ps_idx,
+                         max_per_image: int):
+    """bioem_score_gathered_pairs: ln sum_d L for every listed (image, parameter set), [nnz] float64."""
+    torch = _torch()
+    o = _dev_tensor(offsets, torch.int32, ctx.device, "offsets", ndim=1)
+    p = _dev_tensor(ps_idx, torch.int32, ctx.device, "ps_idx", ndim=1)
+    out = torch.empty(p.shape[0], dtype=torch.float64, device=ctx.device)
+    _check(ctx, lib().bioem_score_gathered_pairs(ctx._h, images._h, projset._h, int(max_shift), _ptr(o), _ptr(p),
+                                                 p.shape[0], int(max_per_image), _ptr(out)), "score_gathered_pairs")
+    return out
+
+
 def acc_logP(ctx: Context, acc, log_norm: float):
     torch = _torch()
     a = _dev_tensor(acc, torch.float64, ctx.device, "acc", ndim=2, last=2)

@@ -52,6 +52,8 @@ SIGNATURES = {
     "bioem_score_gathered": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_int, c_int, c_void_p,
                                      c_int]),
     "bioem_acc_logP": (c_int, [c_void_p, c_void_p, c_int, c_double, c_void_p]),
+    "bioem_score_gathered_pairs": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_int, c_int,
+                                           c_void_p]),
     "bioem_score_accumulate": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int]),
     "bioem_ensemble": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_int, c_void_p]),
     "bioem_cnn_create": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_int, c_ull, ctypes.POINTER(c_void_p)]),

@@ -1406,9 +1406,23 @@ __global__ void k_acc_logP(const double* __restrict__ acc, int n_img, double log
     if (w < n_img) logP[w] = acc[2 * w] + log(acc[2 * w + 1]) - log_norm;
 }
 
+// Per listed pair i of image w: ln sum_d L(w | ps_idx[i], d) = kA + kB + c1 t_min + ln s (one block per image).
+__global__ void __launch_bounds__(kRedThreads) k_gathered_pairs_out(const int* __restrict__ offsets,
+                                                                    const int* __restrict__ ps_idx,
+                                                                    const float* __restrict__ rec_t,
+                                                                    const float* __restrict__ rec_s,
+                                                                    const double* __restrict__ kA,
+                                                                    const double* __restrict__ kB, double c1,
+                                                                    double* __restrict__ pair_lse) {
+    const int w = blockIdx.x;
+    const int b0 = offsets[w], b1 = offsets[w + 1];
+    for (int i = b0 + threadIdx.x; i < b1; i += blockDim.x)
+        pair_lse[i] = kA[w] + kB[ps_idx[i]] + c1 * (double)rec_t[i] + log((double)rec_s[i]);
+}
+
 template <class C>
 int run_gathered(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, int max_shift, const int* offsets,
-                 const int* ps_idx, int nnz, int max_per_image, double* acc, int first) {
+                 const int* ps_idx, int nnz, int max_per_image, double* acc, int first, double* pair_lse) {
     const int n_img = im->n_img;
     const size_t need = (size_t)nnz * 12;
     if (ctx->rec_bytes < need) {
@@ -1444,8 +1458,12 @@ int run_gathered(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps
         if (rc) return rc;
     }
     bioem_launch_begin(ctx, KID_REDUCE_WAVE);
-    k_fold_gathered<<<n_img, kRedThreads, 0, ctx->stream>>>(offsets, ps_idx, rec_t, rec_s, im->d_kA, ps->d_kB,
-                                                           0.5 * (3.0 - (double)n), acc, first);
+    if (pair_lse)
+        k_gathered_pairs_out<<<n_img, kRedThreads, 0, ctx->stream>>>(offsets, ps_idx, rec_t, rec_s, im->d_kA, ps->d_kB,
+                                                                    0.5 * (3.0 - (double)n), pair_lse);
+    else
+        k_fold_gathered<<<n_img, kRedThreads, 0, ctx->stream>>>(offsets, ps_idx, rec_t, rec_s, im->d_kA, ps->d_kB,
+                                                               0.5 * (3.0 - (double)n), acc, first);
     bioem_launch_end(ctx, KID_REDUCE_WAVE);
     return bioem_check_cuda(ctx, cudaGetLastError(), "k_fold_gathered");
 }
@@ -1454,10 +1472,11 @@ int run_gathered(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps
 
 extern "C" {
 
-int bioem_score_gathered(bioem_ctx* ctx, const bioem_images* images, const bioem_projset* projset, int max_shift,
-                         const int* d_offsets, const int* d_ps_idx, int nnz, int max_per_image, double* d_acc,
-                         int first) {
-    if (!ctx || !images || !projset || !d_offsets || !d_acc || nnz < 0 || max_per_image < 0 || (nnz > 0 && !d_ps_idx))
+static int gathered(bioem_ctx* ctx, const bioem_images* images, const bioem_projset* projset, int max_shift,
+                    const int* d_offsets, const int* d_ps_idx, int nnz, int max_per_image, double* d_acc, int first,
+                    double* d_pair_lse) {
+    if (!ctx || !images || !projset || !d_offsets || (!d_acc && !d_pair_lse) || nnz < 0 || max_per_image < 0 ||
+        (nnz > 0 && !d_ps_idx))
         return BIOEM_ERR_INVALID_ARG;
     if (images->ctx != ctx || projset->ctx != ctx || images->nx != projset->nx)
         return bioem_set_error(ctx, BIOEM_ERR_INVALID_ARG, "images and projections do not match");
@@ -1466,15 +1485,30 @@ int bioem_score_gathered(bioem_ctx* ctx, const bioem_images* images, const bioem
                                images->nx);
     if (images->n_img == 0) return BIOEM_OK;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return bioem_set_error(ctx, BIOEM_ERR_CUDA, "cudaSetDevice");
+#define G(C) run_gathered<C>(ctx, images, projset, max_shift, d_offsets, d_ps_idx, nnz, max_per_image, d_acc, first, d_pair_lse)
     switch (images->nx) {
-        case 32: return run_gathered<C32_4>(ctx, images, projset, max_shift, d_offsets, d_ps_idx, nnz, max_per_image, d_acc, first);
-        case 64: return max_shift <= 4 ? run_gathered<C64_4>(ctx, images, projset, max_shift, d_offsets, d_ps_idx, nnz, max_per_image, d_acc, first)
-                                       : run_gathered<C64_8>(ctx, images, projset, max_shift, d_offsets, d_ps_idx, nnz, max_per_image, d_acc, first);
-        case 96: return run_gathered<C96_12>(ctx, images, projset, max_shift, d_offsets, d_ps_idx, nnz, max_per_image, d_acc, first);
-        case 128: return max_shift <= 4 ? run_gathered<C128_4>(ctx, images, projset, max_shift, d_offsets, d_ps_idx, nnz, max_per_image, d_acc, first)
-                                        : run_gathered<C128_16>(ctx, images, projset, max_shift, d_offsets, d_ps_idx, nnz, max_per_image, d_acc, first);
-        default: return run_gathered<C192_24>(ctx, images, projset, max_shift, d_offsets, d_ps_idx, nnz, max_per_image, d_acc, first);
+        case 32: return G(C32_4);
+        case 64: return max_shift <= 4 ? G(C64_4) : G(C64_8);
+        case 96: return G(C96_12);
+        case 128: return max_shift <= 4 ? G(C128_4) : G(C128_16);
+        default: return G(C192_24);
     }
+#undef G
+}
+
+int bioem_score_gathered(bioem_ctx* ctx, const bioem_images* images, const bioem_projset* projset, int max_shift,
+                         const int* d_offsets, const int* d_ps_idx, int nnz, int max_per_image, double* d_acc,
+                         int first) {
+    if (!d_acc) return BIOEM_ERR_INVALID_ARG;
+    return gathered(ctx, images, projset, max_shift, d_offsets, d_ps_idx, nnz, max_per_image, d_acc, first, nullptr);
+}
+
+int bioem_score_gathered_pairs(bioem_ctx* ctx, const bioem_images* images, const bioem_projset* projset, int max_shift,
+                               const int* d_offsets, const int* d_ps_idx, int nnz, int max_per_image,
+                               double* d_pair_lse) {
+    if (!d_pair_lse && nnz > 0) return BIOEM_ERR_INVALID_ARG;
+    if (nnz == 0) return BIOEM_OK;
+    return gathered(ctx, images, projset, max_shift, d_offsets, d_ps_idx, nnz, max_per_image, nullptr, 0, d_pair_lse);
 }
 
 int bioem_acc_logP(bioem_ctx* ctx, const double* d_acc, int n_img, double log_norm, double* d_logP) {

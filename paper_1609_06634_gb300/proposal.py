@@ -14,7 +14,7 @@ import time
 
 import numpy as np
 
-from . import CNN, Context, acc_logP, prepare_images, project_model, score_gathered, synthetic_maps
+from . import CNN, Context, acc_logP, prepare_images, project_model, score_gathered, score_gathered_pairs, synthetic_maps
 
 
 def _torch():
@@ -151,6 +151,47 @@ def score_cells(ctx: Context, images, atoms_dev, bins: np.ndarray, cfg, wave: in
     torch.cuda.synchronize()
     return {"logP": logp.cpu().numpy(), "evals": evals, "seconds": time.perf_counter() - t0,
             "cells": int(len(used))}
+
+
+def rerank_coarse(ctx: Context, images, atoms_dev, bins: np.ndarray, cfg, keep: int, wave: int = 2304) -> dict:
+    """Exact re-ranking of proposed joint bins: bin (coarse cell, defocus) is scored at the cell's own
+    coarse grid orientation x its defocus x every B (ln sum over B and displacements of L, the
+    closed-form likelihood of the scoring path); per image the `keep` best bins are returned, best
+    first.  The cells are projected in waves of `wave`."""
+    import workloads
+    torch = _torch()
+    dev = ctx.device
+    nd, nb = cfg.n_defocus, len(cfg.bfactors)
+    nctf = nd * nb
+    coarse_q = workloads.hopf_grid(cfg.coarse_level).astype(np.float32)
+    bins = np.asarray(bins, dtype=np.int64)
+    cells, dd = bins // nd, bins % nd
+    scores = np.full(bins.shape, -np.inf)
+    used = np.unique(cells)
+    evals = 0
+    t0 = time.perf_counter()
+    for w0 in range(0, len(used), wave):
+        wc = used[w0:w0 + wave]
+        pos = np.full(cfg.n_coarse, -1, dtype=np.int64)
+        pos[wc] = np.arange(len(wc))
+        ps = project_model(ctx, atoms_dev, cfg.sigma_A, torch.from_numpy(np.ascontiguousarray(coarse_q[wc])).to(dev),
+                           cfg.ctf_rows(), cfg.npix, cfg.pixel_A)
+        pc = pos[cells]
+        mask = pc >= 0                                   # [n_img, K]: bins of this wave
+        base = (pc * nctf + dd * nb)[mask]               # row-major: grouped by image
+        flat = (base[:, None] + np.arange(nb)[None, :]).ravel()
+        counts = mask.sum(axis=1) * nb
+        off = torch.from_numpy(np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)).to(dev)
+        v = score_gathered_pairs(ctx, images, ps, cfg.max_shift, off,
+                                 torch.from_numpy(flat.astype(np.int32)).to(dev), max(1, int(counts.max())))
+        v = v.cpu().numpy().reshape(-1, nb)
+        m = v.max(axis=1)
+        scores[mask] = m + np.log(np.exp(v - m[:, None]).sum(axis=1))
+        evals += int(counts.sum())
+        ps.close()
+    order = np.argsort(-scores, axis=1, kind="stable")[:, :keep]
+    return {"bins": np.take_along_axis(bins, order, axis=1), "evals": evals,
+            "seconds": time.perf_counter() - t0}
 
 
 def all_bins(n_img: int, cfg) -> np.ndarray:

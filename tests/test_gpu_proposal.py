@@ -75,3 +75,39 @@ def test_proposal_end_to_end(env):
     truth = inf["label_q"].astype(np.int64) * cfg.n_defocus + inf["label_d"]
     recall = np.mean([t in b for t, b in zip(truth, bins)])
     assert recall > cfg.top_k / n_joint
+    # exact re-ranking of a 4x wider proposal at the coarse grid points, keeping top_k bins
+    big = net.propose(x, 4 * cfg.top_k)[0].cpu().numpy().astype(np.int64)
+    rr = proposal.rerank_coarse(ctx, im, atoms[0], big, cfg, cfg.top_k)
+    assert rr["bins"].shape == bins.shape and rr["evals"] == cfg.n_infer * 4 * cfg.top_k * len(cfg.bfactors)
+    assert all(set(r) <= set(b) for r, b in zip(rr["bins"], big))
+    prop_rr = proposal.score_cells(ctx, im, atoms[0], rr["bins"], cfg)
+    kept_rr = prop_rr["logP"] - full["logP"]
+    recall_rr = np.mean([t in b for t, b in zip(truth, rr["bins"])])
+    print(f"re-ranked: recall {recall_rr:.3f} (network top-k {recall:.3f}); kept mean {np.mean(kept_rr):.3f}")
+    assert recall_rr >= recall - 1.0 / cfg.n_infer
+    assert np.mean(kept_rr) >= np.mean(kept_prop) - 1e-6
+
+
+def test_gathered_pairs_match_score_pairs(env):
+    """Per-pair values of per-image lists equal bioem_score_pairs on the same (image, set) pairs."""
+    import torch
+    bioem, ctx = env
+    import oracle
+    cfg = workloads.get_config("tiny")
+    wl = workloads.workload(cfg, n_img=5)
+    imgs = oracle.synthesize_images(wl)
+    dev = torch.device("cuda", 0)
+    im = bioem.prepare_images(ctx, torch.from_numpy(imgs).to(dev), cfg.pixel_A)
+    ps = bioem.project_model(ctx, torch.from_numpy(wl["atoms"]).to(dev), cfg.sigma_A,
+                             torch.from_numpy(wl["quats"][:40]).to(dev), wl["ctfs"], cfg.npix, cfg.pixel_A)
+    _, plse = bioem.score_pairs(ctx, im, ps, cfg.max_shift)
+    plse = plse.cpu().numpy()
+    rng = np.random.default_rng(8)
+    lists = [np.sort(rng.choice(240, size=n, replace=False)) for n in (1, 37, 0, 240, 100)]
+    off = np.concatenate([[0], np.cumsum([len(x) for x in lists])]).astype(np.int32)
+    flat = np.concatenate(lists).astype(np.int32)
+    got = bioem.score_gathered_pairs(ctx, im, ps, cfg.max_shift, torch.from_numpy(off).to(dev),
+                                     torch.from_numpy(flat).to(dev), 240).cpu().numpy()
+    assert ctx.status() == 0
+    ref = np.concatenate([plse[w, x] for w, x in enumerate(lists)])
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-9)
