@@ -42,9 +42,10 @@ METRIC = "parameter-set×image evals/sec (all shifts) at stated |Δlog P| vs FP6
 UNIT = "evals/s"
 SCORE_SRC = os.path.join(ROOT, "paper_1609_06634_gb300", "csrc", "score.cu")
 
-# DRAM traffic of k_score from an ncu capture, valid only for the kernel source it was taken on.
-# bytes per evaluated pair at the throughput shape; None until a capture of the current source exists.
-K_SCORE_TRAFFIC = {"source_sha256": None, "bytes_per_pair": None}
+# DRAM traffic of k_score from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass,
+# of one full-size launch of this workload: 87,376 parameter sets x 2048 images, 116.89 GB + 2.22 GB),
+# valid only for the kernel source it was taken on; bytes per evaluated pair.
+K_SCORE_TRAFFIC = {"source_sha256": "44f35e2a88bd495b6952288a6367531a066004e05d2db354261d850d0d960acf", "bytes_per_pair": (116.887598e9 + 2.224428e9) / (87376 * 2048)}
 
 
 def parse_args():
