@@ -43,12 +43,9 @@ UNIT = "evals/s"
 SCORE_SRC = os.path.join(ROOT, "paper_1609_06634_gb300", "csrc", "score.cu")
 
 # DRAM traffic of k_score from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass,
-# of one full-size launch of this workload: 87,376 parameter sets x 2048 images, 116.89 GB + 2.22 GB),
+# of one full-size launch of this workload: 87,376 parameter sets x 2048 images, 29.38 GB + 2.21 GB),
 # valid only for the kernel source it was taken on; bytes per evaluated pair.
-# DRAM bytes per launch of k_score_gemm on the precision workloads (64 images x 6912 sets, +-4 px), mean
-# of three one-pass captures per form, valid only for the gemm.cu source they were taken on.
-K_SCORE_GEMM_TRAFFIC = {"source_sha256": "14aa8ab9a39f7c387674c14187d861c0ae31c0dfd34dac84a2f1d46c2fcff5ed", "bytes_per_launch": {'128/bf16x2': 3537586176, '128/fp16x2': 3751961088, '128/bf16x2_real': 3489215573, '128/fp16x2_real': 3822173525, '64/bf16x2': 895058091, '64/fp16x2': 895042645, '64/bf16x2_real': 868144555, '64/fp16x2_real': 868380843}}
-K_SCORE_TRAFFIC = {"source_sha256": "44f35e2a88bd495b6952288a6367531a066004e05d2db354261d850d0d960acf", "bytes_per_pair": (116.887598e9 + 2.224428e9) / (87376 * 2048)}
+K_SCORE_TRAFFIC = {"source_sha256": "b27d77c5f27f256a7d8badfb9de131e8047d5adbac872dc4493e4690d1e3d03b", "bytes_per_pair": (29.377286e9 + 2.210155e9) / (87376 * 2048)}
 
 
 def parse_args():

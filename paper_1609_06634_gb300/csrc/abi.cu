@@ -143,6 +143,7 @@ int bioem_create(bioem_ctx** out, int device, void* cuda_stream) {
     }
     if (!rc && cudaMalloc((void**)&ctx->d_status, sizeof(int)) != cudaSuccess) rc = BIOEM_ERR_OOM;
     if (!rc && cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess) rc = BIOEM_ERR_CUDA;
+    if (!rc && cudaMalloc((void**)&ctx->d_work, 4 * sizeof(int)) != cudaSuccess) rc = BIOEM_ERR_OOM;
     for (int k = 0; k < 5 && !rc; ++k) {
         const int n = kSizes[k];
         float2* h = (float2*)malloc(sizeof(float2) * n);
@@ -184,6 +185,7 @@ void bioem_destroy(bioem_ctx* ctx) {
     if (ctx->d_rec) cudaFree(ctx->d_rec);
     if (ctx->d_acc) cudaFree(ctx->d_acc);
     if (ctx->d_status) cudaFree(ctx->d_status);
+    if (ctx->d_work) cudaFree(ctx->d_work);
     for (int k = 0; k < 5; ++k)
         if (ctx->d_tw[k]) cudaFree(ctx->d_tw[k]);
     for (auto& t : ctx->pending) {

@@ -26,6 +26,7 @@ struct bioem_ctx {
     cudaStream_t stream;
     int num_sms;
     int* d_status;                      // device status word (BIOEM_ERR_* bits folded to a code)
+    int* d_work;                        // work-item counter of the scoring kernel (reset before each launch)
     unsigned long long scratch_limit;   // bytes allowed for per-pair records
     // per-pair record scratch (grown on demand)
     void* d_rec;

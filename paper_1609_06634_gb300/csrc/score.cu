@@ -382,13 +382,23 @@ __device__ __forceinline__ void score_item(unsigned char* smem, const float2* __
     }
 }
 
+// Work items (chunk ci, image w), item = ci n_img + w, are taken in index order from a global counter
+// (zero at launch): the items in flight stay within one or two chunks of parameter sets, so a chunk
+// is read from DRAM about once (a fixed item-per-block assignment let the blocks drift apart over
+// thousands of items until several chunks competed for the L2).
 template <class C>
 __global__ void __launch_bounds__(C::THREADS, 1)
 k_score(const float2* __restrict__ gtw, const float2* __restrict__ img_spec, int n_img,
         const float2* __restrict__ ps_spec, int ps_begin, int ps_count, int chunk, int n_items, int s, float c1,
-        float* __restrict__ rec_t, float* __restrict__ rec_s, int* __restrict__ rec_d, int* __restrict__ status) {
+        float* __restrict__ rec_t, float* __restrict__ rec_s, int* __restrict__ rec_d, int* __restrict__ status,
+        int* __restrict__ work) {
     extern __shared__ __align__(16) unsigned char smem[];
-    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    __shared__ int next_item;
+    for (;;) {
+        if (threadIdx.x == 0) next_item = atomicAdd(work, 1);
+        __syncthreads();
+        const int item = next_item;   // read by every thread before score_item's first barrier
+        if (item >= n_items) break;
         const int ci = item / n_img;
         const int w = item - ci * n_img;
         const int lo = ci * chunk;
@@ -652,9 +662,11 @@ int run_score(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, i
         if (n_items > 0x7fffffffll) return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE, "too many work items");
         const int grid = (int)(n_items < slots ? n_items : slots);
         bioem_launch_begin(ctx, KID_SCORE);
+        if (cudaMemsetAsync(ctx->d_work, 0, sizeof(int), ctx->stream) != cudaSuccess)
+            return bioem_check_cuda(ctx, cudaGetLastError(), "work counter");
         k_score<C><<<grid, C::THREADS, smem, ctx->stream>>>(bioem_twiddles(ctx, C::N), im->d_spec, n_img, ps->d_spec,
                                                              wbegin, wl, (int)chunk, (int)n_items, max_shift, c1f,
-                                                             rec_t, rec_s, rec_d, ctx->d_status);
+                                                             rec_t, rec_s, rec_d, ctx->d_status, ctx->d_work);
         bioem_launch_end(ctx, KID_SCORE);
         return bioem_check_cuda(ctx, cudaGetLastError(), "k_score");
     };
@@ -820,10 +832,12 @@ int run_score_noalloc(bioem_ctx* ctx, const bioem_images* im, const bioem_projse
         const long long n_items = ((wl + chunk - 1) / chunk) * n_img;
         if (n_items > 0x7fffffffll) return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE, "too many work items");
         const int grid = (int)(n_items < slots ? n_items : slots);
+        if (cudaMemsetAsync(ctx->d_work, 0, sizeof(int), ctx->stream) != cudaSuccess)
+            return bioem_check_cuda(ctx, cudaGetLastError(), "work counter");
         k_score<C><<<grid, C::THREADS, smem, ctx->stream>>>(bioem_twiddles(ctx, C::N), im->d_spec, n_img, ps->d_spec,
                                                              (int)w0, wl, (int)chunk,
                                                              (int)n_items, max_shift, c1f, rec_t, rec_s, rec_d,
-                                                             ctx->d_status);
+                                                             ctx->d_status, ctx->d_work);
         ctx->n_launches++;
         ctx->kid_launches[KID_SCORE]++;
         rc = bioem_check_cuda(ctx, cudaGetLastError(), "k_score");
