@@ -385,7 +385,8 @@ __device__ __forceinline__ void score_item(unsigned char* smem, const float2* __
 // Work items (chunk ci, image w), item = ci n_img + w, are taken in index order from a global counter
 // (zero at launch): the items in flight stay within one or two chunks of parameter sets, so a chunk
 // is read from DRAM about once (a fixed item-per-block assignment let the blocks drift apart over
-// thousands of items until several chunks competed for the L2).
+// thousands of items until several chunks competed for the L2; visiting two chunks per image before
+// the next image, to reuse each image, made the two chunks compete the same way).
 template <class C>
 __global__ void __launch_bounds__(C::THREADS, 1)
 k_score(const float2* __restrict__ gtw, const float2* __restrict__ img_spec, int n_img,
@@ -937,9 +938,16 @@ __device__ __forceinline__ int find_seg(const SegDesc* segs, int n, long long x,
 }
 
 __global__ void __launch_bounds__(kMultiThreads, 1)
-k_score_multi(const SegDesc* __restrict__ segs, int n_segs, long long n_items, int* __restrict__ status) {
+k_score_multi(const SegDesc* __restrict__ segs, int n_segs, long long n_items, int* __restrict__ status,
+              unsigned long long* __restrict__ work) {
     extern __shared__ __align__(16) unsigned char smem[];
-    for (long long item = blockIdx.x; item < n_items; item += gridDim.x) {
+    __shared__ long long next_item;
+    for (;;) {
+        // items in index order from a global counter (zero at launch), as in k_score
+        if (threadIdx.x == 0) next_item = (long long)atomicAdd(work, 1ull);
+        __syncthreads();
+        const long long item = next_item;
+        if (item >= n_items) break;
         const int g = find_seg(segs, n_segs, item, false);
         const SegDesc& sd = segs[g];
         const long long local = item - sd.item_begin;
@@ -1049,6 +1057,7 @@ struct bioem_batch {
     std::vector<SegDesc> segs;
     SegDesc* d_segs;
     void* d_rec;
+    unsigned long long* d_work;   // work-item counter of the scoring launch
     long long n_items, n_rows;
     float* d_out;
     cudaStream_t cap_stream;
@@ -1084,6 +1093,8 @@ static int batch_build(bioem_batch* b, int grid_override) {
     if (cudaMalloc((void**)&b->d_segs, nb) != cudaSuccess) return bioem_set_error(ctx, BIOEM_ERR_OOM, "segment table");
     if (cudaMemcpy(b->d_segs, b->segs.data(), nb, cudaMemcpyHostToDevice) != cudaSuccess)
         return bioem_set_error(ctx, BIOEM_ERR_CUDA, "segment table upload");
+    if (cudaMalloc((void**)&b->d_work, sizeof(unsigned long long)) != cudaSuccess)
+        return bioem_set_error(ctx, BIOEM_ERR_OOM, "work counter");
     if (cudaFuncSetAttribute(k_score_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMultiSmem) != cudaSuccess)
         return bioem_set_error(ctx, BIOEM_ERR_CUDA, "shared memory attribute (%zu bytes)", kMultiSmem);
     int per_sm = 0;
@@ -1098,8 +1109,9 @@ static int batch_build(bioem_batch* b, int grid_override) {
         return bioem_set_error(ctx, BIOEM_ERR_CUDA, "capture stream");
     if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return bioem_set_error(ctx, BIOEM_ERR_CUDA, "begin capture");
+    cudaMemsetAsync(b->d_work, 0, sizeof(unsigned long long), b->cap_stream);
     k_score_multi<<<b->grid, kMultiThreads, kMultiSmem, b->cap_stream>>>(b->d_segs, (int)b->segs.size(), b->n_items,
-                                                                        ctx->d_status);
+                                                                        ctx->d_status, b->d_work);
     k_reduce_multi<<<(unsigned)b->n_rows, kRedThreads, 0, b->cap_stream>>>(b->d_segs, (int)b->segs.size(), b->d_out,
                                                                            b->n_cols);
     cudaError_t e = cudaStreamEndCapture(b->cap_stream, &b->graph);
@@ -1178,7 +1190,9 @@ int bioem_autotune(bioem_ctx* ctx, const bioem_images* images, const bioem_projs
         double ms_best_rep = 1e300;
         for (int rep = 0; rep < 3; ++rep) {
             cudaEventRecord(e0, ctx->stream);
-            k_score_multi<<<grid, kMultiThreads, kMultiSmem, ctx->stream>>>(d_seg, 1, b.n_items, ctx->d_status);
+            cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned long long), ctx->stream);
+            k_score_multi<<<grid, kMultiThreads, kMultiSmem, ctx->stream>>>(
+                d_seg, 1, b.n_items, ctx->d_status, reinterpret_cast<unsigned long long*>(ctx->d_work));
             cudaEventRecord(e1, ctx->stream);
             if (cudaEventSynchronize(e1) != cudaSuccess) { rc = bioem_check_cuda(ctx, cudaGetLastError(), "autotune"); break; }
             float ms = 0.f;
@@ -1336,6 +1350,7 @@ void bioem_batch_free(bioem_batch* b) {
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     if (b->d_segs) cudaFree(b->d_segs);
     if (b->d_rec) cudaFree(b->d_rec);
+    if (b->d_work) cudaFree(b->d_work);
     cudaGetLastError();
     delete b;
 }
