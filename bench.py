@@ -43,9 +43,9 @@ UNIT = "evals/s"
 SCORE_SRC = os.path.join(ROOT, "paper_1609_06634_gb300", "csrc", "score.cu")
 
 # DRAM traffic of k_score from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass,
-# of one full-size launch of this workload: 87,376 parameter sets x 2048 images, 29.38 GB + 2.21 GB),
+# of one full-size launch of this workload: 87,376 parameter sets x 2048 images, 29.39 GB + 2.21 GB),
 # valid only for the kernel source it was taken on; bytes per evaluated pair.
-K_SCORE_TRAFFIC = {"source_sha256": "b27d77c5f27f256a7d8badfb9de131e8047d5adbac872dc4493e4690d1e3d03b", "bytes_per_pair": (29.377286e9 + 2.210155e9) / (87376 * 2048)}
+K_SCORE_TRAFFIC = {"source_sha256": "bd22ad191f1cdc58d3b6634b6ce0001c83be633fb799679fb99f43b3d320bc50", "bytes_per_pair": (29.391460e9 + 2.213254e9) / (87376 * 2048)}
 
 
 def parse_args():
