@@ -42,6 +42,9 @@ METRIC = "parameter-set×image evals/sec (all shifts) at stated |Δlog P| vs FP6
 UNIT = "evals/s"
 SCORE_SRC = os.path.join(ROOT, "paper_1609_06634_gb300", "csrc", "score.cu")
 
+# DRAM bytes per launch of k_score_gemm on the precision workloads (64 images x 6912 sets, +-4 px), mean
+# of the one-pass captures of each form's launches, valid only for the gemm.cu source they were taken on.
+K_SCORE_GEMM_TRAFFIC = {"source_sha256": "c077eb2210d57e6d059a1b04ea3fb72797d3c8258f89dab99d405be3b32075f2", "bytes_per_launch": {'128/bf16x2': 3794691556, '128/fp16x2': 5033599431, '128/bf16x2_real': 4005294820, '128/fp16x2_real': 5370143033, '64/bf16x2': 895775374, '64/fp16x2': 896910507, '64/bf16x2_real': 868407154, '64/fp16x2_real': 869934222}}
 # DRAM traffic of k_score from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass,
 # of one full-size launch of this workload: 87,376 parameter sets x 2048 images, 29.39 GB + 2.21 GB),
 # valid only for the kernel source it was taken on; bytes per evaluated pair.

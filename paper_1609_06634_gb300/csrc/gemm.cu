@@ -27,9 +27,10 @@
 // an accumulator into FP32 registers (tcgen05.ld, then round-to-nearest adds) while the next group
 // of K chunks accumulates into the other.  The tensor cores' own FP32 accumulation, run over the
 // whole K of a tile, biased |rho| low by about 1e-5 (log P by -7e-3 at 128 px; one-signed, the
-// same for BF16 and FP16 operands); restarting it every GROUP chunks (48 MMAs) and summing the
-// partial products in registers removes most of that.  Every wait on a barrier is bounded in
-// time; on expiry the kernel sets a status bit and leaves cleanly.
+// same for BF16 and FP16 operands); restarting it every GROUP chunks (96 MMAs) and summing the
+// partial products in registers removes most of that (restarting every 48 MMAs halves the rest but
+// lets the epilogue's likelihood pass stall the MMAs at tile ends: 5-11 % slower).  Every wait on a
+// barrier is bounded in time; on expiry the kernel sets a status bit and leaves cleanly.
 //
 // Operands are stored in global memory already in the tensor cores' shared-memory layout (K-major,
 // no swizzle: 8-row x 16-byte core matrices, the 4 core matrices of a 32-element K chunk 128 B
@@ -56,7 +57,7 @@ constexpr int STAGE = 2 * A_TERM + 2 * B_TERM; // 48 KB: A hi, A lo, B hi, B lo
 constexpr int NSTAGE = 4;
 constexpr int EPI_THREADS = 256;               // epilogue: 8 warps, two per tensor-memory lane quarter
 constexpr int GEMM_THREADS = 64 + EPI_THREADS; // warp 0 copies, warp 1 MMAs, warps 2-9 epilogue
-constexpr int GROUP = 8;                       // K chunks accumulated in tensor memory before a drain (48 MMAs)
+constexpr int GROUP = 16;                      // K chunks accumulated in tensor memory before a drain (96 MMAs)
 constexpr size_t GEMM_SMEM = (size_t)NSTAGE * STAGE + 256;
 constexpr int TMEM_COLS = 2 * GN;
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per barrier wait
