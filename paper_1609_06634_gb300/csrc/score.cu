@@ -29,6 +29,9 @@
 namespace {
 
 constexpr int L = 16;   // sub-transform length
+// Dynamic shared memory a scoring block may take: 227 KiB per block, less 1 KiB for the kernels'
+// static shared variables.
+constexpr size_t kScoreSmemLimit = 227u * 1024u - 1024u;
 
 // W_M^t = exp(+2 pi i t / M), uploaded once per device.
 __constant__ float2 c_w16[16];
@@ -113,7 +116,7 @@ __host__ __device__ constexpr int bitrev(int u, int bits) {
 __host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
 __host__ __device__ constexpr int pmod(int a, int m) { return ((a % m) + m) % m; }
 
-template <int N_, int SMAX_, int PB_, int THREADS_>
+template <int N_, int SMAX_, int PB_, int THREADS_, bool ALLOW_PACK_ = true>
 struct Cfg {
     static constexpr int N = N_;
     static constexpr int SMAX = SMAX_;
@@ -123,7 +126,6 @@ struct Cfg {
     static constexpr int NS = 2 * SMAX + 1;    // displacements per axis
     static constexpr int NROW = 2 * SMAX;      // stage-B transform rows per pair (dy < SMAX)
     static constexpr int R = N / L;            // sub-sequences per transform
-    static constexpr int TASKS_A = PB * H;     // stage-A column tasks per batch
     static constexpr int THREADS = THREADS_;   // threads doing the work (a block may have more)
     static constexpr int NWARPS = THREADS / 32;  // full warps (combine step)
     static_assert(THREADS >= PB * NROW, "one stage-B row per thread");
@@ -136,28 +138,49 @@ struct Cfg {
     static constexpr size_t SM_TWC = (size_t)R * NS * sizeof(float2);
     static constexpr size_t SM_ROW = (size_t)PB * NROW * (2 * sizeof(float) + sizeof(int));
     static constexpr size_t SM_DIR = (size_t)NDIR * sizeof(float);
-    static constexpr size_t SMEM = SM_IMG + SM_Q + SM_TWC + SM_ROW + SM_DIR;
+    static constexpr size_t SM_BASE = SM_IMG + SM_Q + SM_TWC + SM_ROW + SM_DIR;
+    // Packed edge columns: for real images and projections the product conj(O) C is Hermitian in
+    // ky on the kx = 0 and kx = N/2 columns, so both columns' stage-A outputs are real, and one
+    // complex transform of Z(ky) = P(ky, 0) + i P(ky, N/2) gives Q(dy, 0) as its real part and
+    // Q(dy, N/2) as its imaginary part.  That leaves N/2 column tasks per pair (a multiple of the
+    // block's warps); Z is formed for the batch in shared memory before stage A.  Used where Z fits.
+    static constexpr size_t SM_Z_PACKED = (size_t)PB * N * sizeof(float2);
+    static constexpr bool PACK = ALLOW_PACK_ && SM_BASE + SM_Z_PACKED <= kScoreSmemLimit;
+    static constexpr int NCOL = PACK ? NC : H;      // stage-A column tasks per pair
+    static constexpr int TASKS_A = PB * NCOL;       // stage-A column tasks per batch
+    static constexpr size_t SM_Z = PACK ? SM_Z_PACKED : 0;
+    static constexpr size_t SMEM = SM_BASE + SM_Z;
+    static_assert(SMEM <= kScoreSmemLimit, "dynamic shared memory per block");
 };
 
 // Stage A for one column kx of one pair: Q(dy, kx) for dy = -SMAX..SMAX, with the rows ky = b + R a
 // of sub-sequence b transformed by an in-register FFT and recombined with the twiddles
 // twc[b][m] = W_N^(b (m - SMAX)) (shared memory, the same address for every thread: broadcast).
-// The projection column is read from global memory one sub-sequence ahead of its use.
+// The projection column is read from global memory one sub-sequence ahead of its use.  With zcol
+// set (the packed edge columns) the inputs are zcol[ky] instead of the product.
 template <class C>
 __device__ __forceinline__ void stage_a_column(float2 (&acc)[C::NS], const float2* __restrict__ img_col,
-                                               const float2* __restrict__ ps_col, const float2* __restrict__ twc) {
+                                               const float2* __restrict__ ps_col, const float2* __restrict__ twc,
+                                               const float2* __restrict__ zcol) {
     constexpr int H = C::H, R = C::R, NS = C::NS, SMAX = C::SMAX;
     float2 cn[L];
+    if (!zcol) {
 #pragma unroll
-    for (int a = 0; a < L; ++a) cn[a] = __ldg(ps_col + (R * a) * H);
+        for (int a = 0; a < L; ++a) cn[a] = __ldg(ps_col + (R * a) * H);
+    }
 #pragma unroll 1
     for (int b = 0; b < R; ++b) {
         float2 x[L];
+        if (zcol) {
 #pragma unroll
-        for (int a = 0; a < L; ++a) x[a] = c_mulc(img_col[(R * a) * H], cn[a]);
-        if (b + 1 < R) {
+            for (int a = 0; a < L; ++a) x[a] = zcol[R * a + b];
+        } else {
 #pragma unroll
-            for (int a = 0; a < L; ++a) cn[a] = __ldg(ps_col + (R * a + 1) * H);
+            for (int a = 0; a < L; ++a) x[a] = c_mulc(img_col[(R * a) * H], cn[a]);
+            if (b + 1 < R) {
+#pragma unroll
+                for (int a = 0; a < L; ++a) cn[a] = __ldg(ps_col + (R * a + 1) * H);
+            }
         }
         img_col += H;
         ps_col += H;
@@ -249,7 +272,7 @@ __device__ __forceinline__ void score_tail(const float2* __restrict__ q_s, const
 #pragma unroll
         for (int m = 0; m < NS; ++m) acc[m] = 0.f;
         stage_b_row<C>(acc, qrow, twc_s);
-        const float qn = qrow[NC].x;   // Nyquist column, weight 1, phase (-1)^dx
+        const float qn = C::PACK ? qrow[0].y : qrow[NC].x;   // Nyquist column, weight 1, phase (-1)^dx
         const bool row_ok = abs(r - SMAX) <= s;
         float tmin = INFINITY;
         int arg = 0x7fffffff;
@@ -291,7 +314,8 @@ __device__ __forceinline__ void score_tail(const float2* __restrict__ q_s, const
                 idx += step;
                 idx -= (idx >= N) ? N : 0;
             }
-            const float rho = qrow[0].x + 2.f * accv + ((dx & 1) ? -qrow[NC].x : qrow[NC].x);
+            const float qn = C::PACK ? qrow[0].y : qrow[NC].x;
+            const float rho = qrow[0].x + 2.f * accv + ((dx & 1) ? -qn : qn);
             const bool ok = SMAX <= s && abs(dx) <= s;
             dir_t[i] = ok ? loglik_t(rho, status) : INFINITY;
         }
@@ -338,7 +362,8 @@ __device__ __forceinline__ void score_item(unsigned char* smem, const float2* __
     float2* img_s = reinterpret_cast<float2*>(smem);
     float2* q_s = reinterpret_cast<float2*>(smem + C::SM_IMG);
     float2* twc_s = reinterpret_cast<float2*>(smem + C::SM_IMG + C::SM_Q);
-    float* row_t = reinterpret_cast<float*>(twc_s + C::R * NS);
+    float2* z_s = twc_s + C::R * NS;   // [PB][N] packed edge columns (C::PACK)
+    float* row_t = reinterpret_cast<float*>(z_s + (C::PACK ? C::PB * N : 0));
     float* row_s = row_t + C::PB * NROW;
     int* row_d = reinterpret_cast<int*>(row_s + C::PB * NROW);
     float* dir_t = reinterpret_cast<float*>(row_d + C::PB * NROW);
@@ -359,19 +384,33 @@ __device__ __forceinline__ void score_item(unsigned char* smem, const float2* __
     }
     __syncthreads();
     for (int p0 = lo; p0 < hi; p0 += C::PB) {
+        // ---------------- packed edge columns Z(ky) = P(ky, 0) + i P(ky, N/2) of the batch's pairs
+        if constexpr (C::PACK) {
+            for (int i = tid; i < C::PB * N; i += blockDim.x) {
+                const int j = i / N;
+                const int ky = i - j * N;
+                const int p = min(p0 + j, hi - 1);
+                const int gp = ps_idx ? __ldg(ps_idx + p) : ps_begin + p;
+                const float2* ps_row = ps_spec + (size_t)gp * N * H + (size_t)ky * H;
+                const float2 e0 = c_mulc(img_s[ky * H], __ldg(ps_row));
+                const float2 e1 = c_mulc(img_s[ky * H + NC], __ldg(ps_row + NC));
+                z_s[i] = make_float2(e0.x - e1.y, e0.y + e1.x);
+            }
+            __syncthreads();
+        }
         // ---------------- stage A: one column of one pair per task
         if (active) {
 #pragma unroll 1
             for (int task = tid; task < C::TASKS_A; task += C::THREADS) {
-                const int j = task / H;
-                const int kx = task - j * H;
+                const int j = task / C::NCOL;
+                const int kx = task - j * C::NCOL;
                 const int p = min(p0 + j, hi - 1);
                 const int gp = ps_idx ? __ldg(ps_idx + p) : ps_begin + p;
                 const float2* ps_col = ps_spec + (size_t)gp * N * H + kx;
                 float2 acc[NS];
 #pragma unroll
                 for (int m = 0; m < NS; ++m) acc[m] = make_float2(0.f, 0.f);
-                stage_a_column<C>(acc, img_s + kx, ps_col, twc_s);
+                stage_a_column<C>(acc, img_s + kx, ps_col, twc_s, (C::PACK && kx == 0) ? z_s + j * N : nullptr);
                 float2* qdst = q_s + (size_t)j * NS * C::QS + kx;
 #pragma unroll
                 for (int m = 0; m < NS; ++m) qdst[m * C::QS] = acc[m];
@@ -691,14 +730,22 @@ int run_score_gemm(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* 
     return run_waves(ctx, im, ps, max_shift, max_shift, align, out, records);
 }
 
-// <N, SMAX, pairs per batch, threads>
-using C32_4 = Cfg<32, 4, 32, 272>;
-using C64_4 = Cfg<64, 4, 32, 264>;
-using C64_8 = Cfg<64, 8, 16, 264>;
-using C96_12 = Cfg<96, 12, 10, 245>;
-using C128_4 = Cfg<128, 4, 32, 260>;
-using C128_16 = Cfg<128, 16, 8, 260>;
+// <N, SMAX, pairs per batch, threads>: the threads divide the stage-A tasks (PB N/2 with the packed
+// edge columns, PB (N/2 + 1) without) into whole rounds; 256 threads are eight full warps, two per
+// scheduler.
+using C32_4 = Cfg<32, 4, 32, 256>;
+using C64_4 = Cfg<64, 4, 32, 256>;
+using C64_8 = Cfg<64, 8, 16, 256>;
+using C96_12 = Cfg<96, 12, 10, 240>;
+using C128_4 = Cfg<128, 4, 24, 256>;
+using C128_16 = Cfg<128, 16, 8, 256>;
 using C192_24 = Cfg<192, 24, 2, 194>;
+static_assert(C32_4::PACK && C64_4::PACK && C64_8::PACK && C96_12::PACK && C128_4::PACK && C128_16::PACK,
+              "packed edge columns fit");
+static_assert(C128_16::TASKS_A % C128_16::THREADS == 0 && C128_4::TASKS_A % C128_4::THREADS == 0 &&
+              C64_8::TASKS_A % C64_8::THREADS == 0 && C64_4::TASKS_A % C64_4::THREADS == 0 &&
+              C32_4::TASKS_A % C32_4::THREADS == 0 && C96_12::TASKS_A % C96_12::THREADS == 0 &&
+              C192_24::TASKS_A % C192_24::THREADS == 0, "whole stage-A rounds");
 
 }  // namespace
 
@@ -899,10 +946,12 @@ extern "C" int bioem_score_noalloc(bioem_ctx* ctx, const bioem_images* images, c
 
 namespace {
 
-using M64 = Cfg<64, 8, 15, 256>;
-using M96 = Cfg<96, 12, 10, 256>;
-using M128 = Cfg<128, 16, 7, 256>;
-using M192 = Cfg<192, 24, 2, 256>;
+// (unpacked edge columns: the four instances share one kernel's registers, and with the packed
+// columns they spill)
+using M64 = Cfg<64, 8, 15, 256, false>;
+using M96 = Cfg<96, 12, 10, 256, false>;
+using M128 = Cfg<128, 16, 7, 256, false>;
+using M192 = Cfg<192, 24, 2, 256, false>;
 constexpr int kMultiThreads = 256;
 
 constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
