@@ -84,8 +84,8 @@ __device__ __forceinline__ void dif_butterflies(float2 (&x)[LL]) {
     if constexpr (BLK < LL) {
         if constexpr (J < HALF) {
             const float2 a = x[BLK + J], b = x[BLK + J + HALF];
-            x[BLK + J] = c_add(a, b);
-            x[BLK + J + HALF] = twiddle_mul<LL, J * (LL / (2 * HALF))>(c_sub(a, b));
+            x[BLK + J] = __fadd2_rn(a, b);
+            x[BLK + J + HALF] = twiddle_mul<LL, J * (LL / (2 * HALF))>(__ffma2_rn(b, make_float2(-1.f, -1.f), a));
             dif_butterflies<LL, HALF, BLK, J + 1>(x);
         } else {
             dif_butterflies<LL, HALF, BLK + 2 * HALF, 0>(x);
@@ -106,6 +106,22 @@ __device__ __forceinline__ void dif_stages(float2 (&x)[LL]) {
 template <int LL>
 __device__ __forceinline__ void fft_dif(float2 (&x)[LL]) {
     dif_stages<LL, LL / 2>(x);
+}
+
+template <int LL, int J>
+__device__ __forceinline__ void first_stage_half_zero(float2 (&x)[LL]) {
+    if constexpr (J < LL / 2) {
+        x[J + LL / 2] = twiddle_mul<LL, J>(x[J]);
+        first_stage_half_zero<LL, J + 1>(x);
+    }
+}
+
+// fft_dif for inputs whose upper half x[LL/2 ..] is zero: the first stage's butterflies reduce to
+// copies (a + 0 = a, a - 0 = a).
+template <int LL>
+__device__ __forceinline__ void fft_dif_half_zero(float2 (&x)[LL]) {
+    first_stage_half_zero<LL, 0>(x);
+    dif_stages<LL, LL / 4>(x);
 }
 
 __host__ __device__ constexpr int bitrev(int u, int bits) {
@@ -208,9 +224,7 @@ __device__ __forceinline__ void stage_b_row(float (&acc)[C::NS], const float2* _
 #pragma unroll
         for (int a = 0; a < L / 2; ++a) x[a] = c_scale(qrow[b + R * a], 2.f);
         if (b == 0) x[0] = make_float2(qrow[0].x, 0.f);   // kx = 0: weight 1, real
-#pragma unroll
-        for (int a = L / 2; a < L; ++a) x[a] = make_float2(0.f, 0.f);
-        fft_dif<L>(x);
+        fft_dif_half_zero<L>(x);
         const float2* tw = twc + b * NS;
 #pragma unroll
         for (int mi = 0; mi < NS; ++mi) {
@@ -369,7 +383,6 @@ __device__ __forceinline__ void score_item(unsigned char* smem, const float2* __
     float* dir_t = reinterpret_cast<float*>(row_d + C::PB * NROW);
 
     const int tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5;
     const bool active = tid < C::THREADS;
     __syncthreads();   // the previous item's readers of shared memory are done
     {
