@@ -46,9 +46,9 @@ SCORE_SRC = os.path.join(ROOT, "paper_1609_06634_gb300", "csrc", "score.cu")
 # of the one-pass captures of each form's launches, valid only for the gemm.cu source they were taken on.
 K_SCORE_GEMM_TRAFFIC = {"source_sha256": "c077eb2210d57e6d059a1b04ea3fb72797d3c8258f89dab99d405be3b32075f2", "bytes_per_launch": {'128/bf16x2': 3794691556, '128/fp16x2': 5033599431, '128/bf16x2_real': 4005294820, '128/fp16x2_real': 5370143033, '64/bf16x2': 895775374, '64/fp16x2': 896910507, '64/bf16x2_real': 868407154, '64/fp16x2_real': 869934222}}
 # DRAM traffic of k_score from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass,
-# of one full-size launch of this workload: 87,376 parameter sets x 2048 images, 29.39 GB + 2.21 GB),
+# of one full-size launch of this workload: 87,376 parameter sets x 2048 images, 29.35 GB + 2.20 GB),
 # valid only for the kernel source it was taken on; bytes per evaluated pair.
-K_SCORE_TRAFFIC = {"source_sha256": "bd22ad191f1cdc58d3b6634b6ce0001c83be633fb799679fb99f43b3d320bc50", "bytes_per_pair": (29.391460e9 + 2.213254e9) / (87376 * 2048)}
+K_SCORE_TRAFFIC = {"source_sha256": "cba5213eed8b33ca5d746cadb8c67af3cb4df22ceb85fda66eee095b05bf436e", "bytes_per_pair": (29.352918e9 + 2.202553e9) / (87376 * 2048)}
 
 
 def parse_args():

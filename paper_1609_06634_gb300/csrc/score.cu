@@ -708,7 +708,7 @@ int run_score(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, i
         long long per_img = (target_items + n_img - 1) / n_img;
         long long chunk = (wl + per_img - 1) / per_img;
         chunk = ((chunk + C::PB - 1) / C::PB) * C::PB;
-        if (chunk > 512) chunk = 512;
+        if (chunk > 512) chunk = 512 / C::PB * C::PB;
         if (chunk < C::PB) chunk = C::PB;
         const long long n_chunks = (wl + chunk - 1) / chunk;
         const long long n_items = n_chunks * n_img;
@@ -743,18 +743,19 @@ int run_score_gemm(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* 
     return run_waves(ctx, im, ps, max_shift, max_shift, align, out, records);
 }
 
-// <N, SMAX, pairs per batch, threads>: the threads divide the stage-A tasks (PB N/2 with the packed
-// edge columns, PB (N/2 + 1) without) into whole rounds; 256 threads are eight full warps, two per
-// scheduler.
-using C32_4 = Cfg<32, 4, 32, 256>;
-using C64_4 = Cfg<64, 4, 32, 256>;
-using C64_8 = Cfg<64, 8, 16, 256>;
-using C96_12 = Cfg<96, 12, 10, 240>;
+// <N, SMAX, pairs per batch, threads[, packed edge columns allowed]>: the threads divide the
+// stage-A tasks (PB N/2 with the packed edge columns, PB (N/2 + 1) without) into whole rounds.
+// Packed edge columns where they measured faster (128 px: 2 % at s = 4, 6 % at s = 16); at 32-96
+// px the transforms are short enough that forming Z costs about as much as the column it saves
+// (unpacked 4-9 % faster there).
+using C32_4 = Cfg<32, 4, 32, 272, false>;
+using C64_4 = Cfg<64, 4, 32, 264, false>;
+using C64_8 = Cfg<64, 8, 16, 264, false>;
+using C96_12 = Cfg<96, 12, 10, 245, false>;
 using C128_4 = Cfg<128, 4, 24, 256>;
 using C128_16 = Cfg<128, 16, 8, 256>;
 using C192_24 = Cfg<192, 24, 2, 194>;
-static_assert(C32_4::PACK && C64_4::PACK && C64_8::PACK && C96_12::PACK && C128_4::PACK && C128_16::PACK,
-              "packed edge columns fit");
+static_assert(C128_4::PACK && C128_16::PACK, "packed edge columns fit");
 static_assert(C128_16::TASKS_A % C128_16::THREADS == 0 && C128_4::TASKS_A % C128_4::THREADS == 0 &&
               C64_8::TASKS_A % C64_8::THREADS == 0 && C64_4::TASKS_A % C64_4::THREADS == 0 &&
               C32_4::TASKS_A % C32_4::THREADS == 0 && C96_12::TASKS_A % C96_12::THREADS == 0 &&
@@ -888,7 +889,7 @@ int run_score_noalloc(bioem_ctx* ctx, const bioem_images* im, const bioem_projse
         const long long per_img = (4ll * slots + n_img - 1) / n_img;
         long long chunk = (wl + per_img - 1) / per_img;
         chunk = ((chunk + C::PB - 1) / C::PB) * C::PB;
-        if (chunk > 512) chunk = 512;
+        if (chunk > 512) chunk = 512 / C::PB * C::PB;
         if (chunk < C::PB) chunk = C::PB;
         const long long n_items = ((wl + chunk - 1) / chunk) * n_img;
         if (n_items > 0x7fffffffll) return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE, "too many work items");
@@ -1533,7 +1534,7 @@ int run_gathered(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score_gathered<C>, C::THREADS, smem);
     if (per_sm < 1) per_sm = 1;
-    int chunk = 256;
+    const int chunk = 256 / C::PB * C::PB;   // whole batches
     const int cpi = (max_per_image + chunk - 1) / chunk;
     const long long items = (long long)n_img * cpi;
     const int grid = (int)(items < (long long)per_sm * ctx->num_sms ? items : (long long)per_sm * ctx->num_sms);
