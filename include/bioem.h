@@ -59,7 +59,8 @@ typedef struct {
  * transform twiddle tables.  *out is set only on success. */
 int bioem_create(bioem_ctx** out, int device, void* cuda_stream);
 
-/* Change the stream later calls enqueue on. */
+/* Change the stream later calls enqueue on.  Handles made earlier keep the stream that was
+ * current when they were made for their release (bioem_free_images / bioem_free_projset). */
 int bioem_set_stream(bioem_ctx* ctx, void* cuda_stream);
 
 /* Upper bound (bytes) on the per-pair record buffer bioem_score uses; larger parameter sets
@@ -301,13 +302,20 @@ void bioem_cnn_free(bioem_cnn* cnn);
  * context's stream around every launch; bioem_kernel_time synchronises the stream and returns the
  * summed device time (ms) and the launch count of one kernel, by name: "k_prepare_images",
  * "k_project", "k_ctf_table", "k_psf_spectra", "k_psf_real", "k_score", "k_reduce_wave",
- * "k_finalize", "k_pairs_out".  bioem_reset_kernel_stats zeroes both. */
+ * "k_finalize", "k_pairs_out", "k_gemm_ops", "k_score_gemm", "k_ensemble".  bioem_reset_kernel_stats
+ * zeroes both. */
 int bioem_set_kernel_timing(bioem_ctx* ctx, int enable);
 int bioem_kernel_time(bioem_ctx* ctx, const char* kernel, double* total_ms, unsigned long long* launches);
 int bioem_reset_kernel_stats(bioem_ctx* ctx);
 unsigned long long bioem_launch_count(const bioem_ctx* ctx);
 
-/* Handle queries and release. */
+/* Handle queries (the number of images / parameter sets; -1 for NULL) and release.
+ * bioem_free_images / bioem_free_projset release the handle's device memory (spectra, per-item
+ * constants and any cached split-precision operands) with stream-ordered frees on the stream that
+ * was current in its context when the handle was made; work that reads the handle on another
+ * stream must be ordered before that stream first.  A handle may be released before or after
+ * its context is destroyed, but is used only with its own context while that context lives.
+ * NULL is a no-op. */
 int bioem_images_count(const bioem_images* images);
 int bioem_projset_count(const bioem_projset* projset);
 void bioem_free_images(bioem_images* images);
