@@ -132,7 +132,7 @@ __host__ __device__ constexpr int bitrev(int u, int bits) {
 __host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
 __host__ __device__ constexpr int pmod(int a, int m) { return ((a % m) + m) % m; }
 
-template <int N_, int SMAX_, int PB_, int THREADS_, bool ALLOW_PACK_ = true>
+template <int N_, int SMAX_, int PB_, int THREADS_, bool ALLOW_PACK_ = true, int BSPLIT_ = 1>
 struct Cfg {
     static constexpr int N = N_;
     static constexpr int SMAX = SMAX_;
@@ -144,6 +144,12 @@ struct Cfg {
     static constexpr int R = N / L;            // sub-sequences per transform
     static constexpr int THREADS = THREADS_;   // threads doing the work (a block may have more)
     static constexpr int NWARPS = THREADS / 32;  // full warps (combine step)
+    // stage-B threads per row: 2 when the block has two threads for every row (each sums half
+    // of the sub-sequences, the halves are exchanged by a lane shuffle, and each evaluates the
+    // likelihood for half of the dx outputs)
+    static constexpr int BSPLIT = BSPLIT_;
+    static_assert((BSPLIT == 1 || BSPLIT == 2) && THREADS >= PB * 2 * SMAX_ * BSPLIT, "stage-B threads");
+    static constexpr bool PREFETCH = THREADS <= 320;   // stage-A projection prefetch (registers)
     static_assert(THREADS >= PB * NROW, "one stage-B row per thread");
     static_assert(NWARPS >= 1, "at least one full warp");
     static_assert(N % L == 0, "sub-transform length divides N");
@@ -152,7 +158,7 @@ struct Cfg {
     static constexpr size_t SM_IMG = (size_t)N * H * sizeof(float2);
     static constexpr size_t SM_Q = (size_t)PB * NS * QS * sizeof(float2);
     static constexpr size_t SM_TWC = (size_t)R * NS * sizeof(float2);
-    static constexpr size_t SM_ROW = (size_t)PB * NROW * (2 * sizeof(float) + sizeof(int));
+    static constexpr size_t SM_ROW = (size_t)PB * NROW * BSPLIT * (2 * sizeof(float) + sizeof(int));
     static constexpr size_t SM_DIR = (size_t)NDIR * sizeof(float);
     static constexpr size_t SM_BASE = SM_IMG + SM_Q + SM_TWC + SM_ROW + SM_DIR;
     // Packed edge columns: for real images and projections the product conj(O) C is Hermitian in
@@ -180,9 +186,11 @@ __device__ __forceinline__ void stage_a_column(float2 (&acc)[C::NS], const float
                                                const float2* __restrict__ zcol) {
     constexpr int H = C::H, R = C::R, NS = C::NS, SMAX = C::SMAX;
     float2 cn[L];
-    if (!zcol) {
+    if constexpr (C::PREFETCH) {
+        if (!zcol) {
 #pragma unroll
-        for (int a = 0; a < L; ++a) cn[a] = __ldg(ps_col + (R * a) * H);
+            for (int a = 0; a < L; ++a) cn[a] = __ldg(ps_col + (R * a) * H);
+        }
     }
 #pragma unroll 1
     for (int b = 0; b < R; ++b) {
@@ -190,13 +198,16 @@ __device__ __forceinline__ void stage_a_column(float2 (&acc)[C::NS], const float
         if (zcol) {
 #pragma unroll
             for (int a = 0; a < L; ++a) x[a] = zcol[R * a + b];
-        } else {
+        } else if constexpr (C::PREFETCH) {
 #pragma unroll
             for (int a = 0; a < L; ++a) x[a] = c_mulc(img_col[(R * a) * H], cn[a]);
             if (b + 1 < R) {
 #pragma unroll
                 for (int a = 0; a < L; ++a) cn[a] = __ldg(ps_col + (R * a + 1) * H);
             }
+        } else {
+#pragma unroll
+            for (int a = 0; a < L; ++a) x[a] = c_mulc(img_col[(R * a) * H], __ldg(ps_col + (R * a) * H));
         }
         img_col += H;
         ps_col += H;
@@ -216,10 +227,10 @@ __device__ __forceinline__ void stage_a_column(float2 (&acc)[C::NS], const float
 // only a < L/2 carries data (kx < N/2 for every b < R).
 template <class C>
 __device__ __forceinline__ void stage_b_row(float (&acc)[C::NS], const float2* __restrict__ qrow,
-                                            const float2* __restrict__ twc) {
+                                            const float2* __restrict__ twc, int b0, int b1) {
     constexpr int R = C::R, NS = C::NS, SMAX = C::SMAX;
 #pragma unroll 1
-    for (int b = 0; b < R; ++b) {
+    for (int b = b0; b < b1; ++b) {
         float2 x[L];
 #pragma unroll
         for (int a = 0; a < L / 2; ++a) x[a] = c_scale(qrow[b + R * a], 2.f);
@@ -277,25 +288,41 @@ __device__ __forceinline__ void score_tail(const float2* __restrict__ q_s, const
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const bool active = tid < C::THREADS;
-    // ---------------- stage B: one row (dy = -SMAX .. SMAX-1) of one pair per thread
-    if (tid < C::PB * NROW) {
-        const int j = tid / NROW;
-        const int r = tid - j * NROW;
+    // ---------------- stage B: one row (dy = -SMAX .. SMAX-1) of one pair per thread (per two
+    // adjacent threads with BSPLIT = 2)
+    if (tid < C::PB * NROW * C::BSPLIT) {
+        constexpr int BS = C::BSPLIT;
+        static_assert(BS == 1 || (C::PB * NROW * BS) % 32 == 0, "split rows fill whole warps");
+        const int rr = tid / BS;
+        const int h = tid - rr * BS;
+        const int j = rr / NROW;
+        const int r = rr - j * NROW;
         const float2* qrow = q_s + ((size_t)j * NS + r) * C::QS;
         float acc[NS];
 #pragma unroll
         for (int m = 0; m < NS; ++m) acc[m] = 0.f;
-        stage_b_row<C>(acc, qrow, twc_s);
+        stage_b_row<C>(acc, qrow, twc_s, h * (C::R / BS), (h + 1) * (C::R / BS));
+        constexpr int MH = BS == 2 ? (NS + 1) / 2 : NS;   // outputs evaluated by this thread
+        int m0 = 0;
+        if constexpr (BS == 2) {
+#pragma unroll
+            for (int m = 0; m < NS; ++m) acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], 1);
+            // the second thread moves its outputs m = MH .. NS-1 to acc[0 ..]
+#pragma unroll
+            for (int i = 0; i < MH; ++i) acc[i] = h ? (i + MH < NS ? acc[i + MH] : 0.f) : acc[i];
+            m0 = h * MH;
+        }
         const float qn = C::PACK ? qrow[0].y : qrow[NC].x;   // Nyquist column, weight 1, phase (-1)^dx
         const bool row_ok = abs(r - SMAX) <= s;
         float tmin = INFINITY;
         int arg = 0x7fffffff;
 #pragma unroll
-        for (int m = 0; m < NS; ++m) {
-            const float rho = acc[m] + (((m - SMAX) & 1) ? -qn : qn);
-            const bool ok = row_ok && abs(m - SMAX) <= s;
+        for (int i = 0; i < MH; ++i) {
+            const int m = m0 + i;
+            const float rho = acc[i] + (((m - SMAX) & 1) ? -qn : qn);
+            const bool ok = row_ok && m < NS && abs(m - SMAX) <= s;
             const float t = ok ? loglik_t(rho, status) : INFINITY;
-            acc[m] = t;
+            acc[i] = t;
             if (t < tmin) {
                 tmin = t;
                 arg = r * NS + m;
@@ -303,7 +330,7 @@ __device__ __forceinline__ void score_tail(const float2* __restrict__ q_s, const
         }
         float ssum = 0.f;
 #pragma unroll
-        for (int m = 0; m < NS; ++m) ssum += (acc[m] < INFINITY) ? __expf(c1 * (acc[m] - tmin)) : 0.f;
+        for (int i = 0; i < MH; ++i) ssum += (acc[i] < INFINITY) ? __expf(c1 * (acc[i] - tmin)) : 0.f;
         row_t[tid] = tmin;
         row_s[tid] = ssum;
         row_d[tid] = arg;
@@ -313,7 +340,7 @@ __device__ __forceinline__ void score_tail(const float2* __restrict__ q_s, const
     // threads with a row get two
     if (active) {
 #pragma unroll 1
-        for (int i = (tid + C::THREADS - C::PB * NROW) % C::THREADS; i < C::NDIR; i += C::THREADS) {
+        for (int i = (tid + C::THREADS - C::PB * NROW * C::BSPLIT) % C::THREADS; i < C::NDIR; i += C::THREADS) {
             const int j = i / NS;
             const int mi = i - j * NS;
             const int dx = mi - SMAX;
@@ -340,8 +367,9 @@ __device__ __forceinline__ void score_tail(const float2* __restrict__ q_s, const
         const int p = p0 + j;
         if (p >= hi) continue;
         Part acc{INFINITY, 0.f, 0x7fffffff};
-        for (int r = lane; r < NROW; r += 32)
-            acc = merge(acc, Part{row_t[j * NROW + r], row_s[j * NROW + r], row_d[j * NROW + r]}, c1);
+        constexpr int NR = NROW * C::BSPLIT;
+        for (int r = lane; r < NR; r += 32)
+            acc = merge(acc, Part{row_t[j * NR + r], row_s[j * NR + r], row_d[j * NR + r]}, c1);
         for (int mi = lane; mi < NS; mi += 32) {
             const float t = dir_t[j * NS + mi];
             acc = merge(acc, Part{t, t < INFINITY ? 1.f : 0.f, 2 * SMAX * NS + mi}, c1);
@@ -378,9 +406,9 @@ __device__ __forceinline__ void score_item(unsigned char* smem, const float2* __
     float2* twc_s = reinterpret_cast<float2*>(smem + C::SM_IMG + C::SM_Q);
     float2* z_s = twc_s + C::R * NS;   // [PB][N] packed edge columns (C::PACK)
     float* row_t = reinterpret_cast<float*>(z_s + (C::PACK ? C::PB * N : 0));
-    float* row_s = row_t + C::PB * NROW;
-    int* row_d = reinterpret_cast<int*>(row_s + C::PB * NROW);
-    float* dir_t = reinterpret_cast<float*>(row_d + C::PB * NROW);
+    float* row_s = row_t + C::PB * NROW * C::BSPLIT;
+    int* row_d = reinterpret_cast<int*>(row_s + C::PB * NROW * C::BSPLIT);
+    float* dir_t = reinterpret_cast<float*>(row_d + C::PB * NROW * C::BSPLIT);
 
     const int tid = threadIdx.x;
     const bool active = tid < C::THREADS;
@@ -753,7 +781,10 @@ using C64_4 = Cfg<64, 4, 32, 264, false>;
 using C64_8 = Cfg<64, 8, 16, 264, false>;
 using C96_12 = Cfg<96, 12, 10, 245, false>;
 using C128_4 = Cfg<128, 4, 24, 256>;
-using C128_16 = Cfg<128, 16, 8, 256>;
+// 128 px, s <= 16: 512 threads (four warps per scheduler, 128 registers), one stage-A column per
+// thread and two threads per stage-B row; 11 % faster than 256 threads with one row per thread,
+// which left the kernel waiting on dependent-instruction latency at two warps per scheduler.
+using C128_16 = Cfg<128, 16, 8, 512, true, 2>;
 using C192_24 = Cfg<192, 24, 2, 194>;
 static_assert(C128_4::PACK && C128_16::PACK, "packed edge columns fit");
 static_assert(C128_16::TASKS_A % C128_16::THREADS == 0 && C128_4::TASKS_A % C128_4::THREADS == 0 &&
