@@ -180,6 +180,9 @@ def bench_reference(args):
     imgs = oracle.synthesize_images(wl)
     quats = wl["quats"][:nq]
     evals = n_img * nq * len(wl["ctfs"])
+    # the workload the GPU arm runs (its config); each step here is the bounded sample above
+    full_img = args.n_img or cfg.n_img
+    full_q = len(wl["quats"]) if args.n_quat is None else min(args.n_quat, len(wl["quats"]))
     for _ in range(args.warmup):
         run_cpu_oracle(imgs, wl["atoms"], quats, wl["ctfs"], cfg)
     t0 = time.perf_counter()
@@ -193,7 +196,7 @@ def bench_reference(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(cfg, n_img, len(quats) * len(wl["ctfs"])),
+            "config": workload_config(cfg, full_img, full_q * len(wl["ctfs"])),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": NCORES, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
