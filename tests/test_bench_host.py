@@ -1,5 +1,6 @@
 """bench.py on the host (no GPU): every global name its functions use is defined, the recorded
-traffic tables are well formed, and the algorithmic work per evaluation is what DESIGN states."""
+traffic tables are well formed, the algorithmic work per evaluation is the stated one, and the
+oracle arm (--impl reference) prints its one line on rank 0 only, with the GPU arm's workload config."""
 import builtins
 import importlib
 import os
@@ -55,3 +56,37 @@ def test_traffic_tables_and_work_per_eval():
                                           for m in ("bf16x2", "fp16x2", "bf16x2_real", "fp16x2_real")}
     # 6 H + 2.5 n log2 n + 4 S at 128 px, S = 1089: 0.628 Mflop
     assert abs(bench.flops_per_eval(128, 16) - 627716.0) < 1.0
+
+
+def _run_reference(env_extra):
+    import json
+    import subprocess
+    env = dict(os.environ, **env_extra)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0", "--cpu-images", "1", "--cpu-quats", "2"],
+                       capture_output=True, text=True, env=env, cwd=ROOT, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip()]
+    return [json.loads(l) for l in lines]
+
+
+def test_reference_arm_line():
+    """The oracle arm prints one line with the GPU arm's workload config and its own sample."""
+    (line,) = _run_reference({"RANK": "0", "WORLD_SIZE": "1"})
+    bench = _bench()
+    import workloads
+    cfg = workloads.get_config("throughput")
+    wl = workloads.workload(cfg, n_img=0)
+    assert line["impl"] == "reference"
+    assert line["metric"] == bench.METRIC and line["unit"] == bench.UNIT and line["higher_is_better"] is True
+    assert line["config"] == bench.workload_config(cfg, cfg.n_img, len(wl["quats"]) * len(wl["ctfs"]))
+    assert line["value"] > 0 and line["steps"] == 1 and line["warmup"] == 0
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1
+    assert cb["sample"].startswith("1 images x 2 orientations")
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_are_silent():
+    assert _run_reference({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
