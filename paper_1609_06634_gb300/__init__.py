@@ -65,7 +65,14 @@ def ctf_array(ctfs) -> ctypes.Array:
 
 
 class Context:
-    """A library context on one CUDA device, enqueueing on a CUDA stream (default: torch's current)."""
+    """A library context on one CUDA device, enqueueing on a CUDA stream.
+
+    The stream defaults to torch's current stream at creation.  Every call enqueues on it, reading
+    its input tensors and writing its output tensors (allocated on torch's current stream) there.
+    While that is torch's current stream, ordinary stream order makes this safe.  When it is not,
+    the caller orders it: ``ctx.stream.wait_stream(torch.cuda.current_stream())`` before a call
+    whose inputs were just produced, and the reverse before reading results or freeing inputs.
+    """
 
     def __init__(self, device=0, stream=None):
         torch = _torch()
