@@ -1,6 +1,7 @@
 """bench.py on the host (no GPU): every global name its functions use is defined, the recorded
-traffic tables are well formed, the algorithmic work per evaluation is the stated one, and the
-oracle arm (--impl reference) prints its one line on rank 0 only, with the GPU arm's workload config."""
+traffic tables are well formed, the algorithmic work per evaluation is the stated one, the
+oracle arm (--impl reference) prints its one line on rank 0 only, with the GPU arm's workload config,
+and the CPU context leg (the paper's FP32 Fourier variant) computes the oracle's log P."""
 import builtins
 import importlib
 import os
@@ -90,3 +91,20 @@ def test_reference_arm_line():
 
 def test_reference_arm_other_ranks_are_silent():
     assert _run_reference({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
+
+
+def test_cpu_fft_context_matches_oracle():
+    """The context leg (the paper's FP32 Fourier variant on the host) computes the oracle's log P."""
+    import numpy as np
+    import oracle
+    import workloads
+    bench = _bench()
+    cfg = workloads.get_config("tiny")
+    wl = workloads.workload(cfg, n_img=4)
+    imgs = oracle.synthesize_images(wl)
+    quats = wl["quats"][:16]
+    projs = oracle.projections(wl["atoms"], quats, wl["ctfs"], cfg.sigma_A, cfg.npix, cfg.pixel_A)
+    ref = oracle.score(imgs, wl["atoms"], quats, wl["ctfs"], cfg.sigma_A, cfg.pixel_A, cfg.max_shift, projs=projs)
+    logp, seconds, threads = bench.run_cpu_fft_context(imgs, projs, cfg.max_shift, reps=2)
+    assert seconds > 0 and threads >= 1
+    np.testing.assert_allclose(logp, ref["logP"], rtol=0, atol=1e-4)
