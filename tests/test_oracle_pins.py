@@ -74,6 +74,27 @@ def test_closed_form_matches_quadrature(npix, seed):
     assert abs(closed - quad) <= 1e-8 * max(1.0, abs(quad)), (closed, quad)
 
 
+@pytest.mark.parametrize("n,seed", [(16, 4), (400, 5), (16384, 6)])
+def test_closed_form_zero_mean_projection_special_case(n, seed):
+    """With sum c = 0 the residual splits as sum (o' - N c)^2 + n (o_mean + mu)^2 (o' = o - o_mean),
+    so the three integrals are textbook ones, at any image size (quadrature needs tiny n):
+    mu gives sqrt(2 pi lambda^2 / n), N gives sqrt(2 pi lambda^2 / C_cc) with the minimum residual
+    R = sum o'^2 - (sum o' c)^2 / C_cc, and int_0^inf lambda^(2-n) exp(-R / 2 lambda^2) d lambda =
+    Gamma((n-3)/2) (R/2)^((3-n)/2) / 2."""
+    rng = np.random.default_rng(seed)
+    c = rng.standard_normal(n)
+    c -= c.mean()
+    o = 0.7 * c + 2.5 + rng.standard_normal(n)
+    op = o - o.mean()
+    c_cc = float(np.sum(c * c))
+    r = float(np.sum(op * op) - np.sum(op * c) ** 2 / c_cc)
+    want = ((1 - n / 2) * math.log(2 * math.pi) - 0.5 * math.log(n * c_cc) - math.log(2.0)
+            + math.lgamma((n - 3) / 2) + (3 - n) / 2 * math.log(r / 2))
+    c_o, c_oo = float(o.sum()), float(np.sum(o * o))
+    got = float(oracle.closed_form_loglik(c_o, c_oo, float(c.sum()), c_cc, float(np.sum(o * c)), n))
+    assert abs(got - want) <= 1e-9 * max(1.0, abs(want)), (got, want)
+
+
 # ---------------------------------------------------------------- transforms and correlation
 def test_dft_pair_matches_numpy():
     rng = np.random.default_rng(7)
