@@ -50,3 +50,14 @@ def test_package_has_no_cpu_path():
     src = open(pkg.__file__).read()
     assert "oracle" not in src.replace("no CPU path", "")
     assert "import numpy" in src   # host-side marshalling of CTF rows only
+
+
+def test_timing_hook_names_match_the_header():
+    """The kernel names bioem_kernel_time accepts (the library's table) are the ones the header lists."""
+    src = open(os.path.join(ROOT, "paper_1609_06634_gb300", "csrc", "abi.cu")).read()
+    table = re.search(r"bioem_kernel_names\[KID_COUNT\]\s*=\s*\{(.*?)\};", src, flags=re.S).group(1)
+    accepted = set(re.findall(r'"(k_[a-z_]+)"', table))
+    hdr = open(os.path.join(ROOT, "include", "bioem.h")).read()
+    doc = re.search(r"bioem_kernel_time synchronises(.*?)\*/", hdr, flags=re.S).group(1)
+    documented = set(re.findall(r'"(k_[a-z_]+)"', doc))
+    assert accepted and accepted == documented, (accepted ^ documented)
