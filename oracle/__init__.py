@@ -1,7 +1,8 @@
 """FP64 CPU oracle of the BioEM scoring path — TEST INFRASTRUCTURE ONLY.
 
-Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
-``bench.py`` may import this package.  The product (``paper_1609_06634_gb300``)
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU legs of ``bench.py``
+(the oracle baseline, the inputs of its CPU context leg, ``--impl reference``)
+may import this package.  The product (``paper_1609_06634_gb300``)
 never imports it, and this package never imports the product: the two share
 no code.  Inputs both sides use come from ``workloads`` (seeded draws only).
 
