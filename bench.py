@@ -405,8 +405,8 @@ def bench_ours(args):
                   "gpu_launches": int(launches), "clocks": clk,
                   "kernel_ms_per_step": {k: v / args.steps for k, v in kernel_ms.items()}}
 
-        # CPU oracle on a bounded sample of the same workload, and the GPU's |d log P| on it
-        if not args.no_cpu:
+        # CPU oracle on a bounded sample of the same workload, and the GPU's |d log P| on it (N = 1 only)
+        if not args.no_cpu and world == 1:
             ni = min(args.cpu_images, n_img)
             nq = min(args.cpu_quats, len(quats_np))
             sample_imgs = images_d[:ni].cpu().numpy()
