@@ -193,10 +193,13 @@ int bioem_synthetic_maps(bioem_ctx* ctx, const float* d_atoms, int n_atoms, doub
  * [n_img] float64 device.  Its scratch (per-image accumulators and per-pair records) is one
  * 16 MiB array that the library reserves statically on every GPU it is loaded on, until the
  * process exits; parameter sets are processed in as many passes as that array requires.
- *   Limit: n_img * (32 + 12 * nctf) bytes, rounded up to 256, must fit in 16 MiB, else
+ *   Limit: round_up(32 * n_img, 256) + 12 * n_img * nctf bytes must fit in 16 MiB, else
  *          BIOEM_ERR_UNSUPPORTED_SIZE with the sizes in bioem_last_error().
- *   The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- *   that device current; make that first call before any stream capture.
+ *   Every call made outside a stream capture looks up the array's device address
+ *   (cudaGetSymbolAddress) with the device current, so a device reset between calls is
+ *   tolerated; a call made while the context's stream is capturing reuses the address of the
+ *   last such lookup.  So make the first call on a device before any stream capture (a first
+ *   call made during a capture returns BIOEM_ERR_INVALID_ARG).
  *   Every call uses the same array and leaves its contents behind (each call initialises what it
  *   reads).  Calls whose work overlaps on the GPU (other streams, other host threads or
  *   contexts) race on the array and corrupt each other's results: serialise them.
@@ -230,6 +233,14 @@ void bioem_batch_free(bioem_batch* batch);
 int bioem_autotune(bioem_ctx* ctx, const bioem_images* images, const bioem_projset* projset, int max_shift,
                    const char* cache_path, int* out_chunk);
 
+/* Load an autotune cache file into this process's table without tuning (no device work).  Only
+ * lines "npix shift chunk" with npix in {64, 96, 128, 192}, 0 <= shift <= npix/8 and chunk a
+ * positive multiple of the batched instance's pairs per batch, at most 4096, are taken; any other
+ * non-blank line is skipped (bioem_autotune then tunes that case afresh and rewrites the file with
+ * valid lines only).  *n_taken / *n_skipped (either may be NULL) receive the counts.
+ * Errors: INVALID_ARG (NULL path, or the file cannot be opened). */
+int bioem_autotune_load(const char* cache_path, int* n_taken, int* n_skipped);
+
 /* Scoring of per-image lists of parameter sets (the paper has no counterpart: it scores every
  * image on the full grid; this serves proposals that restrict each image to a few grid cells).
  * Image w is scored against projset sets d_ps_idx[d_offsets[w] .. d_offsets[w+1]) (CSR, device
@@ -243,6 +254,21 @@ int bioem_score_gathered(bioem_ctx* ctx, const bioem_images* images, const bioem
                          const int* d_offsets, const int* d_ps_idx, int nnz, int max_per_image, double* d_acc,
                          int first);
 int bioem_acc_logP(bioem_ctx* ctx, const double* d_acc, int n_img, double log_norm, double* d_logP);
+
+/* Merge of accumulators of disjoint parts of a grid (Eq. 9's sum split over chunks of parameter
+ * sets, or over the ranks of a sharded scan): d_parts [n_parts][n][2] float64 device, each
+ * (M, S) with ln sum L = M + ln S (an empty part has M = -inf, S = 0); writes the (M, S) of the
+ * union to d_out [n][2] float64 device, folding the parts in index order with
+ * (M, S) + (M', S') = (m, S e^{M - m} + S' e^{M' - m}), m = max(M, M') (deterministic).  d_out
+ * may be d_parts (the first part is overwritten).  Errors: INVALID_ARG, CUDA. */
+int bioem_acc_merge(bioem_ctx* ctx, const double* d_parts, int n_parts, int n, double* d_out);
+
+/* Log-sum-exp of consecutive groups: d_out[g] = ln sum_{j < group_len} exp(d_values[g group_len + j])
+ * for g < n_groups (float64 device arrays, max-shifted; a group of -inf gives -inf).  Serves sums
+ * of Eq. 9 over a few grid points, e.g. ln sum over the B-factors of one orientation and defocus of
+ * the per-pair values of bioem_score_gathered_pairs.  Errors: INVALID_ARG, CUDA. */
+int bioem_group_logsumexp(bioem_ctx* ctx, const double* d_values, long long n_groups, int group_len,
+                          double* d_out);
 
 /* Per-pair values of the same per-image lists (for re-ranking candidates): d_pair_lse [nnz] float64
  * device, d_pair_lse[i] = ln sum_d L(w | d_ps_idx[i], d) for the image w whose list holds entry i.
@@ -297,12 +323,22 @@ int bioem_cnn_train_step(bioem_cnn* cnn, const float* d_images, const int* d_lab
 int bioem_propose(bioem_cnn* cnn, const float* d_images, int n, int k, int* d_bins, float* d_scores);
 void bioem_cnn_free(bioem_cnn* cnn);
 
+/* CUDA-core fused multiply-add throughput of the context's GPU (a measurement hook with no
+ * counterpart in the paper: the denominator of the FP32 scoring form's roofline).  kind 0: FP32
+ * fmaf, 1: FP32 packed pairs (__ffma2_rn), 2: FP64 fma.  Every SM is filled with threads running
+ * 16 independent chains; `reps` timed launches of ~20 ms each (after a calibration launch) on the
+ * context's stream, best kept, in flop/s (2 per multiply-add) in *flops_per_s.  Changes no clock
+ * or other device setting: the figure is at whatever SM clock the device runs.
+ * Errors: INVALID_ARG, CUDA. */
+int bioem_fma_peak(bioem_ctx* ctx, int kind, int reps, double* flops_per_s);
+
 /* Measurement hooks.  bioem_launch_count: kernels the library has launched with this context
  * since creation or the last reset.  With timing enabled, CUDA events are recorded on the
  * context's stream around every launch; bioem_kernel_time synchronises the stream and returns the
  * summed device time (ms) and the launch count of one kernel, by name: "k_prepare_images",
  * "k_project", "k_ctf_table", "k_psf_spectra", "k_psf_real", "k_score", "k_reduce_wave",
- * "k_finalize", "k_pairs_out", "k_gemm_ops", "k_score_gemm", "k_ensemble".  bioem_reset_kernel_stats
+ * "k_finalize", "k_pairs_out", "k_gemm_ops", "k_score_gemm", "k_ensemble", "k_lse_merge".
+ * bioem_reset_kernel_stats
  * zeroes both. */
 int bioem_set_kernel_timing(bioem_ctx* ctx, int enable);
 int bioem_kernel_time(bioem_ctx* ctx, const char* kernel, double* total_ms, unsigned long long* launches);

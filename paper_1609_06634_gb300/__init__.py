@@ -15,7 +15,8 @@ from . import _native
 from ._native import CTF
 
 __all__ = ["BioEMError", "Context", "Images", "ProjSet", "prepare_images", "project_model", "score", "score_all",
-           "best_params", "score_pairs", "score_noalloc", "Batch", "autotune", "CNN", "score_gathered", "acc_logP", "synthetic_maps", "ctf_array", "lib"]
+           "best_params", "score_pairs", "score_noalloc", "Batch", "autotune", "autotune_load", "CNN", "score_gathered", "acc_logP",
+           "acc_merge", "group_logsumexp", "fma_peak", "synthetic_maps", "ctf_array", "lib"]
 
 OK = 0
 ERR_INVALID_ARG, ERR_UNSUPPORTED_SIZE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NUMERIC = -1, -2, -3, -4, -5, -6
@@ -314,6 +315,15 @@ def autotune(ctx: Context, images: Images, projset: ProjSet, max_shift: int, cac
     return out.value
 
 
+def autotune_load(cache_path: str) -> tuple[int, int]:
+    """bioem_autotune_load: (entries taken, lines skipped) of an autotune cache file (no GPU work)."""
+    taken, skipped = ctypes.c_int(0), ctypes.c_int(0)
+    code = lib().bioem_autotune_load(cache_path.encode(), ctypes.byref(taken), ctypes.byref(skipped))
+    if code != OK:
+        raise BioEMError(code, f"autotune_load: cannot read {cache_path}")
+    return taken.value, skipped.value
+
+
 class CNN:
     """bioem_cnn: the learned orientation / defocus proposal network (own CUDA kernels)."""
 
@@ -428,6 +438,45 @@ def acc_logP(ctx: Context, acc, log_norm: float):
     out = torch.empty(a.shape[0], dtype=torch.float64, device=ctx.device)
     _check(ctx, lib().bioem_acc_logP(ctx._h, _ptr(a), a.shape[0], float(log_norm), _ptr(out)), "acc_logP")
     return out
+
+
+def acc_merge(ctx: Context, parts, out=None):
+    """bioem_acc_merge: the (M, S) accumulators of the union of disjoint grid parts.
+
+    ``parts``: [n_parts, n, 2] (or [n, 2] for a single part) float64 device tensor; returns [n, 2]."""
+    torch = _torch()
+    p = _dev_tensor(parts, torch.float64, ctx.device, "parts")
+    if p.dim() == 2:
+        p = p.unsqueeze(0)
+    if p.dim() != 3 or p.shape[2] != 2:
+        raise BioEMError(ERR_INVALID_ARG, "parts must be [n_parts, n, 2]")
+    if out is None:
+        out = torch.empty((p.shape[1], 2), dtype=torch.float64, device=ctx.device)
+    o = _dev_tensor(out, torch.float64, ctx.device, "out", ndim=2, last=2)
+    if o.data_ptr() != out.data_ptr() or o.shape[0] != p.shape[1]:
+        raise BioEMError(ERR_INVALID_ARG, "out must be a contiguous [n, 2] float64 tensor")
+    _check(ctx, lib().bioem_acc_merge(ctx._h, _ptr(p), p.shape[0], p.shape[1], _ptr(out)), "acc_merge")
+    return out
+
+
+def group_logsumexp(ctx: Context, values, group_len: int):
+    """bioem_group_logsumexp: ln sum exp over consecutive groups of ``group_len`` float64 values."""
+    torch = _torch()
+    v = _dev_tensor(values, torch.float64, ctx.device, "values").reshape(-1)
+    if v.numel() % group_len:
+        raise BioEMError(ERR_INVALID_ARG, "values must hold whole groups")
+    n_groups = v.numel() // group_len
+    out = torch.empty(n_groups, dtype=torch.float64, device=ctx.device)
+    _check(ctx, lib().bioem_group_logsumexp(ctx._h, _ptr(v), n_groups, int(group_len), _ptr(out)), "group_logsumexp")
+    return out
+
+
+def fma_peak(ctx: Context, kind: str = "fp32", reps: int = 5) -> float:
+    """bioem_fma_peak: measured CUDA-core multiply-add throughput, flop/s ("fp32", "fp32x2", "fp64")."""
+    k = {"fp32": 0, "fp32x2": 1, "fp64": 2}[kind]
+    out = ctypes.c_double(0.0)
+    _check(ctx, lib().bioem_fma_peak(ctx._h, k, int(reps), ctypes.byref(out)), "fma_peak")
+    return out.value
 
 
 def score_accumulate(ctx: Context, images: Images, projset: ProjSet, max_shift: int, acc, first: bool):

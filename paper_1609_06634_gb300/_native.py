@@ -49,9 +49,13 @@ SIGNATURES = {
     "bioem_batch_evals": (ctypes.c_longlong, [c_void_p]),
     "bioem_batch_free": (None, [c_void_p]),
     "bioem_autotune": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_char_p, ctypes.POINTER(c_int)]),
+    "bioem_autotune_load": (c_int, [c_char_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
     "bioem_score_gathered": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_int, c_int, c_void_p,
                                      c_int]),
     "bioem_acc_logP": (c_int, [c_void_p, c_void_p, c_int, c_double, c_void_p]),
+    "bioem_acc_merge": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p]),
+    "bioem_group_logsumexp": (c_int, [c_void_p, c_void_p, ctypes.c_longlong, c_int, c_void_p]),
+    "bioem_fma_peak": (c_int, [c_void_p, c_int, c_int, ctypes.POINTER(c_double)]),
     "bioem_score_gathered_pairs": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_int, c_int,
                                            c_void_p]),
     "bioem_score_accumulate": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int]),

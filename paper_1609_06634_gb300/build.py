@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libbioem_gb300.so")
-SOURCES = ["abi.cu", "prep_project.cu", "score.cu", "cnn.cu", "gemm.cu", "ensemble.cu"]
+SOURCES = ["abi.cu", "prep_project.cu", "score.cu", "cnn.cu", "gemm.cu", "ensemble.cu", "peak.cu"]
 HEADERS = [os.path.join(CSRC, "bioem_internal.cuh"), os.path.join(ROOT, "include", "bioem.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC,-O2",

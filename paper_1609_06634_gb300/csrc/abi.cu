@@ -27,7 +27,8 @@ int bioem_check_cuda(bioem_ctx* ctx, cudaError_t e, const char* what) {
 
 const char* const bioem_kernel_names[KID_COUNT] = {
     "k_prepare_images", "k_project", "k_ctf_table", "k_psf_spectra", "k_psf_real",
-    "k_score", "k_reduce_wave", "k_finalize", "k_pairs_out", "k_gemm_ops", "k_score_gemm", "k_ensemble"};
+    "k_score", "k_reduce_wave", "k_finalize", "k_pairs_out", "k_gemm_ops", "k_score_gemm", "k_ensemble",
+    "k_lse_merge"};
 
 void bioem_launch_begin(bioem_ctx* ctx, int kid) {
     if (!ctx->timing) return;

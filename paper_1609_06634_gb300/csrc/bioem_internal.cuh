@@ -11,7 +11,7 @@
 // ------------------------------------------------------------------ kernel accounting
 enum bioem_kernel_id {
     KID_PREPARE = 0, KID_PROJECT, KID_CTF_TABLE, KID_PSF_SPECTRA, KID_PSF_REAL, KID_SCORE, KID_REDUCE_WAVE,
-    KID_FINALIZE, KID_PAIRS_OUT, KID_GEMM_OPS, KID_SCORE_GEMM, KID_ENSEMBLE, KID_COUNT
+    KID_FINALIZE, KID_PAIRS_OUT, KID_GEMM_OPS, KID_SCORE_GEMM, KID_ENSEMBLE, KID_LSE_MERGE, KID_COUNT
 };
 extern const char* const bioem_kernel_names[KID_COUNT];
 

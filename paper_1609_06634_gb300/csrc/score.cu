@@ -717,39 +717,55 @@ int run_waves(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, i
     return BIOEM_OK;
 }
 
-// The FP32 form: k_score<C> writes the records (displacements named in C's compile-time window).
+// Resident blocks of k_score<C> on the whole GPU (sets the kernel's shared-memory attribute).
 template <class C>
-int run_score(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, int max_shift,
-              const bioem_score_out& out) {
-    const int n_img = im->n_img;
+int score_slots(bioem_ctx* ctx, int* slots) {
     const size_t smem = C::SMEM;
     if (cudaFuncSetAttribute(k_score<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return bioem_set_error(ctx, BIOEM_ERR_CUDA, "shared memory attribute (%zu bytes)", smem);
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score<C>, C::THREADS, smem) != cudaSuccess || per_sm < 1)
         return bioem_set_error(ctx, BIOEM_ERR_CUDA, "occupancy query");
-    const int slots = per_sm * ctx->num_sms;
+    *slots = per_sm * ctx->num_sms;
+    return BIOEM_OK;
+}
+
+// One k_score<C> launch writing the records of parameter sets [wbegin, wbegin + wl) for every image.
+// Chunk: enough work items to keep every slot busy, at most 512 parameter sets, whole batches.
+template <class C>
+int launch_score_records(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, int slots, int wbegin,
+                         int wl, int max_shift, float* rec_t, float* rec_s, int* rec_d) {
+    const int n_img = im->n_img;
+    const long long target_items = 4ll * slots;
+    const long long per_img = (target_items + n_img - 1) / n_img;
+    long long chunk = (wl + per_img - 1) / per_img;
+    chunk = ((chunk + C::PB - 1) / C::PB) * C::PB;
+    if (chunk > 512) chunk = 512 / C::PB * C::PB;
+    if (chunk < C::PB) chunk = C::PB;
+    const long long n_chunks = (wl + chunk - 1) / chunk;
+    const long long n_items = n_chunks * n_img;
+    if (n_items > 0x7fffffffll) return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE, "too many work items");
+    const int grid = (int)(n_items < slots ? n_items : slots);
     const float c1f = 0.5f * (3.0f - (float)(C::N * C::N));
+    bioem_launch_begin(ctx, KID_SCORE);
+    if (cudaMemsetAsync(ctx->d_work, 0, sizeof(int), ctx->stream) != cudaSuccess)
+        return bioem_check_cuda(ctx, cudaGetLastError(), "work counter");
+    k_score<C><<<grid, C::THREADS, C::SMEM, ctx->stream>>>(bioem_twiddles(ctx, C::N), im->d_spec, n_img, ps->d_spec,
+                                                            wbegin, wl, (int)chunk, (int)n_items, max_shift, c1f,
+                                                            rec_t, rec_s, rec_d, ctx->d_status, ctx->d_work);
+    bioem_launch_end(ctx, KID_SCORE);
+    return bioem_check_cuda(ctx, cudaGetLastError(), "k_score");
+}
+
+// The FP32 form: k_score<C> writes the records (displacements named in C's compile-time window).
+template <class C>
+int run_score(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, int max_shift,
+              const bioem_score_out& out) {
+    int slots = 0;
+    const int rc = score_slots<C>(ctx, &slots);
+    if (rc) return rc;
     auto records = [&](int wbegin, int wl, float* rec_t, float* rec_s, int* rec_d) -> int {
-        // chunk: enough work items to keep every slot busy, at most 512 parameter sets
-        const long long target_items = 4ll * slots;
-        long long per_img = (target_items + n_img - 1) / n_img;
-        long long chunk = (wl + per_img - 1) / per_img;
-        chunk = ((chunk + C::PB - 1) / C::PB) * C::PB;
-        if (chunk > 512) chunk = 512 / C::PB * C::PB;
-        if (chunk < C::PB) chunk = C::PB;
-        const long long n_chunks = (wl + chunk - 1) / chunk;
-        const long long n_items = n_chunks * n_img;
-        if (n_items > 0x7fffffffll) return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE, "too many work items");
-        const int grid = (int)(n_items < slots ? n_items : slots);
-        bioem_launch_begin(ctx, KID_SCORE);
-        if (cudaMemsetAsync(ctx->d_work, 0, sizeof(int), ctx->stream) != cudaSuccess)
-            return bioem_check_cuda(ctx, cudaGetLastError(), "work counter");
-        k_score<C><<<grid, C::THREADS, smem, ctx->stream>>>(bioem_twiddles(ctx, C::N), im->d_spec, n_img, ps->d_spec,
-                                                             wbegin, wl, (int)chunk, (int)n_items, max_shift, c1f,
-                                                             rec_t, rec_s, rec_d, ctx->d_status, ctx->d_work);
-        bioem_launch_end(ctx, KID_SCORE);
-        return bioem_check_cuda(ctx, cudaGetLastError(), "k_score");
+        return launch_score_records<C>(ctx, im, ps, slots, wbegin, wl, max_shift, rec_t, rec_s, rec_d);
     };
     return run_waves(ctx, im, ps, max_shift, C::SMAX, ps->nctf, out, records);
 }
@@ -865,17 +881,27 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
 void* g_noalloc_ptr[kMaxDevices] = {};
 
-// Device address of the static scratch on the current device (looked up on first use).
+// Device address of the static scratch on the current device.  Looked up again on every call made
+// outside a stream capture (a device reset between calls reloads the module, possibly at another
+// address); a call made while the stream is capturing uses the address of the last such lookup.
 int noalloc_scratch(bioem_ctx* ctx, void** out) {
     if (ctx->device < 0 || ctx->device >= kMaxDevices)
         return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE, "device ordinal %d too large", ctx->device);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        cs = cudaStreamCaptureStatusActive;   // unknown: do not call into the runtime's module table
+    }
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[ctx->device]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) return bioem_check_cuda(ctx, e != cudaSuccess ? e : cudaErrorInvalidSymbol,
                                                              "cudaGetSymbolAddress(static scoring scratch)");
         g_noalloc_ptr[ctx->device] = p;
+    } else if (!g_noalloc_ptr[ctx->device]) {
+        return bioem_set_error(ctx, BIOEM_ERR_INVALID_ARG,
+                               "allocation-free scoring: the first call on a device must come before any stream capture");
     }
     *out = g_noalloc_ptr[ctx->device];
     return BIOEM_OK;
@@ -904,50 +930,29 @@ int run_score_noalloc(bioem_ctx* ctx, const bioem_images* im, const bioem_projse
     float* rec_s = rec_t + (size_t)n_img * wave;
     int* rec_d = reinterpret_cast<int*>(rec_s + (size_t)n_img * wave);
 
-    const size_t smem = C::SMEM;
-    if (cudaFuncSetAttribute(k_score<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return bioem_set_error(ctx, BIOEM_ERR_CUDA, "shared memory attribute (%zu bytes)", smem);
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_score<C>, C::THREADS, smem) != cudaSuccess || per_sm < 1)
-        return bioem_set_error(ctx, BIOEM_ERR_CUDA, "occupancy query");
-    const int slots = per_sm * ctx->num_sms;
+    int slots = 0;
+    rc = score_slots<C>(ctx, &slots);
+    if (rc) return rc;
     const int n = C::N * C::N;
-    const float c1f = 0.5f * (3.0f - (float)n);
     const double c1 = 0.5 * (3.0 - (double)n);
     const int S = (2 * max_shift + 1) * (2 * max_shift + 1);
     for (long long w0 = 0; w0 < ps->n_ps; w0 += wave) {
         const int wl = (int)(ps->n_ps - w0 < wave ? ps->n_ps - w0 : wave);
-        const long long per_img = (4ll * slots + n_img - 1) / n_img;
-        long long chunk = (wl + per_img - 1) / per_img;
-        chunk = ((chunk + C::PB - 1) / C::PB) * C::PB;
-        if (chunk > 512) chunk = 512 / C::PB * C::PB;
-        if (chunk < C::PB) chunk = C::PB;
-        const long long n_items = ((wl + chunk - 1) / chunk) * n_img;
-        if (n_items > 0x7fffffffll) return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE, "too many work items");
-        const int grid = (int)(n_items < slots ? n_items : slots);
-        if (cudaMemsetAsync(ctx->d_work, 0, sizeof(int), ctx->stream) != cudaSuccess)
-            return bioem_check_cuda(ctx, cudaGetLastError(), "work counter");
-        k_score<C><<<grid, C::THREADS, smem, ctx->stream>>>(bioem_twiddles(ctx, C::N), im->d_spec, n_img, ps->d_spec,
-                                                             (int)w0, wl, (int)chunk,
-                                                             (int)n_items, max_shift, c1f, rec_t, rec_s, rec_d,
-                                                             ctx->d_status, ctx->d_work);
-        ctx->n_launches++;
-        ctx->kid_launches[KID_SCORE]++;
-        rc = bioem_check_cuda(ctx, cudaGetLastError(), "k_score");
+        rc = launch_score_records<C>(ctx, im, ps, slots, (int)w0, wl, max_shift, rec_t, rec_s, rec_d);
         if (rc) return rc;
+        bioem_launch_begin(ctx, KID_REDUCE_WAVE);
         k_reduce_wave<<<n_img, kRedThreads, 0, ctx->stream>>>(rec_t, rec_s, rec_d, im->d_kA, ps->d_kB, (int)w0, wl,
                                                               nctf, ps->nq, c1, log((double)nctf * S), acc, w0 == 0,
                                                               nullptr);
-        ctx->n_launches++;
-        ctx->kid_launches[KID_REDUCE_WAVE]++;
+        bioem_launch_end(ctx, KID_REDUCE_WAVE);
         rc = bioem_check_cuda(ctx, cudaGetLastError(), "k_reduce_wave");
         if (rc) return rc;
     }
+    bioem_launch_begin(ctx, KID_FINALIZE);
     k_finalize<<<(n_img + 255) / 256, 256, 0, ctx->stream>>>(acc, n_img, log((double)ps->n_ps * S), nctf, C::NS,
                                                               C::SMAX, logP, nullptr, nullptr, nullptr, nullptr,
                                                               nullptr);
-    ctx->n_launches++;
-    ctx->kid_launches[KID_FINALIZE]++;
+    bioem_launch_end(ctx, KID_FINALIZE);
     return bioem_check_cuda(ctx, cudaGetLastError(), "k_finalize");
 }
 
@@ -1164,13 +1169,37 @@ struct bioem_batch {
 static std::mutex g_tune_mutex;
 static std::vector<TuneEntry> g_tune;
 
-static int tune_load(const char* path) {
+// An entry the batched launch can use: a batched image size, a shift window its instance covers,
+// and a chunk that is a whole number of that instance's batches, at most 4096 parameter sets.
+static bool tune_entry_valid(int npix, int s, int chunk) {
+    if (npix != 64 && npix != 96 && npix != 128 && npix != 192) return false;
+    if (s < 0 || s > multi_smax(npix) || 2 * s >= npix) return false;
+    const int pb = multi_pb(npix);
+    return chunk > 0 && chunk <= 4096 && chunk % pb == 0;
+}
+
+// Read "npix shift chunk" lines into the process table.  Lines that are not three integers, or
+// whose entry is not valid, are skipped (a corrupted or foreign cache file then only costs a new
+// tuning run); returns the number of entries taken (-1 if the file cannot be opened) and, in
+// *skipped, the number of non-blank lines skipped.
+static int tune_load(const char* path, int* skipped = nullptr) {
+    if (skipped) *skipped = 0;
     FILE* f = fopen(path, "r");
-    if (!f) return 0;
-    int npix, s, chunk, n = 0;
+    if (!f) return -1;
+    char line[256];
+    int n = 0;
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    while (fscanf(f, "%d %d %d", &npix, &s, &chunk) == 3) {
-        if (chunk <= 0 || chunk > 4096) continue;
+    while (fgets(line, sizeof line, f)) {
+        int npix, s, chunk;
+        char extra;
+        const int got = sscanf(line, "%d %d %d %c", &npix, &s, &chunk, &extra);
+        if (got != 3 || !tune_entry_valid(npix, s, chunk)) {
+            bool blank = true;
+            for (const char* c = line; *c; ++c)
+                if (*c != ' ' && *c != '\t' && *c != '\n' && *c != '\r') blank = false;
+            if (!blank && skipped) ++*skipped;
+            continue;
+        }
         bool found = false;
         for (auto& e : g_tune)
             if (e.npix == npix && e.s == s) { e.chunk = chunk; found = true; }
@@ -1216,6 +1245,15 @@ static int batch_build(bioem_batch* b, int grid_override) {
 }
 
 extern "C" {
+
+int bioem_autotune_load(const char* cache_path, int* n_taken, int* n_skipped) {
+    if (!cache_path) return BIOEM_ERR_INVALID_ARG;
+    int skipped = 0;
+    const int n = tune_load(cache_path, &skipped);
+    if (n_taken) *n_taken = n < 0 ? 0 : n;
+    if (n_skipped) *n_skipped = skipped;
+    return n < 0 ? BIOEM_ERR_INVALID_ARG : BIOEM_OK;
+}
 
 int bioem_autotune(bioem_ctx* ctx, const bioem_images* images, const bioem_projset* projset, int max_shift,
                    const char* cache_path, int* out_chunk) {
@@ -1529,6 +1567,41 @@ __global__ void k_acc_logP(const double* __restrict__ acc, int n_img, double log
     if (w < n_img) logP[w] = acc[2 * w] + log(acc[2 * w + 1]) - log_norm;
 }
 
+// Eq. 9's sum over disjoint parts of a grid: out[w] = the (M, S) pair of the union of the n_parts
+// accumulators parts[k][w] (each ln sum L = M + ln S; an empty part has M = -inf), folded in index
+// order k = 0, 1, ... so the result does not depend on the launch.  out may be parts (part 0).
+__global__ void k_acc_merge(const double* __restrict__ parts, int n_parts, int n, double* out) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= n) return;
+    double M = -INFINITY, S = 0.0;
+    for (int k = 0; k < n_parts; ++k) {
+        const double m2 = parts[((size_t)k * n + w) * 2], s2 = parts[((size_t)k * n + w) * 2 + 1];
+        if (!(m2 > -INFINITY)) continue;
+        if (m2 > M) { S = S * exp(M - m2) + s2; M = m2; }
+        else S += s2 * exp(m2 - M);
+    }
+    out[2 * w] = M;
+    out[2 * w + 1] = S;
+}
+
+// out[g] = ln sum_j exp(v[g len + j]) for consecutive groups of len values (a sum of Eq. 9 over a
+// few grid points, e.g. the B-factors of one orientation and defocus), max-shifted in float64.
+__global__ void k_group_lse(const double* __restrict__ v, long long n_groups, int len, double* __restrict__ out) {
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n_groups;
+         g += (long long)gridDim.x * blockDim.x) {
+        const double* x = v + g * len;
+        double m = -INFINITY;
+        for (int j = 0; j < len; ++j) m = fmax(m, x[j]);
+        if (!(m > -INFINITY)) {
+            out[g] = m;
+            continue;
+        }
+        double s = 0.0;
+        for (int j = 0; j < len; ++j) s += exp(x[j] - m);
+        out[g] = m + log(s);
+    }
+}
+
 // Per listed pair i of image w: ln sum_d L(w | ps_idx[i], d) = kA + kB + c1 t_min + ln s (one block per image).
 __global__ void __launch_bounds__(kRedThreads) k_gathered_pairs_out(const int* __restrict__ offsets,
                                                                     const int* __restrict__ ps_idx,
@@ -1632,6 +1705,27 @@ int bioem_score_gathered_pairs(bioem_ctx* ctx, const bioem_images* images, const
     if (!d_pair_lse && nnz > 0) return BIOEM_ERR_INVALID_ARG;
     if (nnz == 0) return BIOEM_OK;
     return gathered(ctx, images, projset, max_shift, d_offsets, d_ps_idx, nnz, max_per_image, nullptr, 0, d_pair_lse);
+}
+
+int bioem_acc_merge(bioem_ctx* ctx, const double* d_parts, int n_parts, int n, double* d_out) {
+    if (!ctx || n_parts < 1 || n < 0 || (n > 0 && (!d_parts || !d_out))) return BIOEM_ERR_INVALID_ARG;
+    if (n == 0) return BIOEM_OK;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return bioem_set_error(ctx, BIOEM_ERR_CUDA, "cudaSetDevice");
+    bioem_launch_begin(ctx, KID_LSE_MERGE);
+    k_acc_merge<<<(n + 255) / 256, 256, 0, ctx->stream>>>(d_parts, n_parts, n, d_out);
+    bioem_launch_end(ctx, KID_LSE_MERGE);
+    return bioem_check_cuda(ctx, cudaGetLastError(), "k_acc_merge");
+}
+
+int bioem_group_logsumexp(bioem_ctx* ctx, const double* d_values, long long n_groups, int group_len, double* d_out) {
+    if (!ctx || n_groups < 0 || group_len < 1 || (n_groups > 0 && (!d_values || !d_out))) return BIOEM_ERR_INVALID_ARG;
+    if (n_groups == 0) return BIOEM_OK;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return bioem_set_error(ctx, BIOEM_ERR_CUDA, "cudaSetDevice");
+    const long long blocks = (n_groups + 255) / 256;
+    bioem_launch_begin(ctx, KID_LSE_MERGE);
+    k_group_lse<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, ctx->stream>>>(d_values, n_groups, group_len, d_out);
+    bioem_launch_end(ctx, KID_LSE_MERGE);
+    return bioem_check_cuda(ctx, cudaGetLastError(), "k_group_lse");
 }
 
 int bioem_acc_logP(bioem_ctx* ctx, const double* d_acc, int n_img, double log_norm, double* d_logP) {

@@ -9,9 +9,9 @@ inputs; a scan started again with the same inputs and checkpoint continues where
 
 Partial accumulators of disjoint parts of the grid (chunks, or the shards of several processes)
 combine with the log-sum-exp operator (M, S) + (M', S') = (m, S e^{M - m} + S' e^{M' - m}),
-m = max(M, M'); `merge_partials` is that operator on host arrays and `allreduce_partials` applies it
-across the ranks of a torch.distributed group (one all-gather: the single exchange step a sharded
-grid needs).
+m = max(M, M'); `merge_partials` applies it on the device through the library (bioem_acc_merge)
+and `allreduce_partials` across the ranks of a torch.distributed group (one all-gather: the single
+exchange step a sharded grid needs, then the library's merge in rank order).
 
 All scoring arithmetic runs in the library's kernels; this module only sequences calls and files.
 """
@@ -23,7 +23,7 @@ import os
 
 import numpy as np
 
-from . import acc_logP, project_model, score_accumulate
+from . import acc_logP, acc_merge, project_model, score_accumulate
 
 
 def _torch():
@@ -59,32 +59,30 @@ def load_checkpoint(path: str, fp: str):
         return z["acc"].copy(), int(z["next_chunk"])
 
 
-def merge_partials(a: np.ndarray, b: np.ndarray) -> np.ndarray:
-    """Log-sum-exp merge of [n, 2] (M, S) accumulators of disjoint parts of a grid."""
-    a = np.asarray(a, dtype=np.float64)
-    b = np.asarray(b, dtype=np.float64)
-    M = np.maximum(a[:, 0], b[:, 0])
-    out = np.empty_like(a)
-    with np.errstate(invalid="ignore"):
-        sa = np.where(np.isfinite(a[:, 0]), a[:, 1] * np.exp(a[:, 0] - M), 0.0)
-        sb = np.where(np.isfinite(b[:, 0]), b[:, 1] * np.exp(b[:, 0] - M), 0.0)
-    out[:, 0] = M
-    out[:, 1] = sa + sb
-    return out
+def merge_partials(ctx, *parts):
+    """(M, S) accumulators [n, 2] (float64 device tensors) of the union of disjoint grid parts,
+    merged by the library in argument order."""
+    torch = _torch()
+    return acc_merge(ctx, torch.stack([p.contiguous() for p in parts]))
 
 
-def allreduce_partials(acc, group=None):
+def allreduce_partials(acc, group=None, ctx=None, merge=None):
     """Merge every rank's [n, 2] (M, S) accumulators (a torch tensor) with one all-gather; each rank
-    gets the merged result.  Works with any torch.distributed backend (gloo on CPU, NCCL on GPUs)."""
+    gets the merged result.  The gathered parts [world, n, 2] are merged in rank order by
+    ``merge(parts)`` when given, else by the library on ``ctx``'s device (bioem_acc_merge).
+    Works with any torch.distributed backend (NCCL on GPUs; gloo on CPU, where the caller supplies
+    ``merge`` because the library runs on GPUs only)."""
     torch = _torch()
     import torch.distributed as dist
     world = dist.get_world_size(group)
     parts = [torch.empty_like(acc) for _ in range(world)]
     dist.all_gather(parts, acc.contiguous(), group=group)
-    merged = parts[0].cpu().numpy()
-    for p in parts[1:]:
-        merged = merge_partials(merged, p.cpu().numpy())
-    return torch.from_numpy(merged).to(acc.device)
+    stacked = torch.stack(parts)
+    if merge is not None:
+        return merge(stacked)
+    if ctx is None:
+        raise ValueError("allreduce_partials: pass the library context (or a merge function)")
+    return acc_merge(ctx, stacked.to(ctx.device))
 
 
 class OrientationScan:

@@ -14,7 +14,8 @@ import time
 
 import numpy as np
 
-from . import CNN, Context, acc_logP, prepare_images, project_model, score_gathered, score_gathered_pairs, synthetic_maps
+from . import (CNN, Context, acc_logP, group_logsumexp, prepare_images, project_model, score_gathered,
+               score_gathered_pairs, synthetic_maps)
 
 
 def _torch():
@@ -184,9 +185,8 @@ def rerank_coarse(ctx: Context, images, atoms_dev, bins: np.ndarray, cfg, keep: 
         off = torch.from_numpy(np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)).to(dev)
         v = score_gathered_pairs(ctx, images, ps, cfg.max_shift, off,
                                  torch.from_numpy(flat.astype(np.int32)).to(dev), max(1, int(counts.max())))
-        v = v.cpu().numpy().reshape(-1, nb)
-        m = v.max(axis=1)
-        scores[mask] = m + np.log(np.exp(v - m[:, None]).sum(axis=1))
+        # ln sum over the B-factors of each bin (the library's log-sum-exp; the host only orders bins)
+        scores[mask] = group_logsumexp(ctx, v, nb).cpu().numpy()
         evals += int(counts.sum())
         ps.close()
     order = np.argsort(-scores, axis=1, kind="stable")[:, :keep]

@@ -61,3 +61,27 @@ def test_timing_hook_names_match_the_header():
     doc = re.search(r"bioem_kernel_time synchronises(.*?)\*/", hdr, flags=re.S).group(1)
     documented = set(re.findall(r'"(k_[a-z_]+)"', doc))
     assert accepted and accepted == documented, (accepted ^ documented)
+
+
+def test_autotune_cache_rejects_corrupted_entries(lib, tmp_path):
+    """Entries for unsupported sizes, windows beyond an instance, chunks that are not whole batches
+    (pairs per batch: 15 / 10 / 7 / 2 at 64 / 96 / 128 / 192 px) or out of range, and malformed
+    lines are skipped; valid ones are taken."""
+    import paper_1609_06634_gb300 as bioem
+    path = tmp_path / "tune.txt"
+    path.write_text("128 16 224\n"        # valid: 32 batches of 7
+                    "64 8 120\n"          # valid
+                    "128 16 5\n"          # not a multiple of 7
+                    "999 4 64\n"          # unsupported size
+                    "128 99 70\n"         # window beyond the 128 px instance
+                    "192 24 0\n"          # empty chunk
+                    "96 12 8000\n"        # above 4096
+                    "64 -1 30\n"          # negative window
+                    "garbage line\n"
+                    "128 4\n"             # too few fields
+                    "128 4 70 extra\n"    # trailing token
+                    "\n")
+    assert bioem.autotune_load(str(path)) == (2, 9)
+    with pytest.raises(bioem.BioEMError):
+        bioem.autotune_load(str(tmp_path / "missing.txt"))
+    assert lib.bioem_autotune_load(None, None, None) == -1

@@ -1,5 +1,6 @@
-"""GPU: 96 / 192 px parity against the oracle, and the batched (graph-captured, multi-segment)
-launch against per-segment bioem_score; the autotuner's choice and cache file."""
+"""GPU: 96 / 192 px parity against the oracle; the batched (graph-captured, multi-segment) launch
+against the oracle and against per-segment bioem_score; the autotuner's choice and cache file,
+including a corrupted cache."""
 import os
 
 import numpy as np
@@ -103,6 +104,30 @@ def test_batch_matches_single_launches(env, batch_case):
     batch.close()
 
 
+def test_batch_matches_oracle(env, batch_case):
+    """The batched log P matrix (one persistent launch over every (model, stack) segment, each item
+    running its size instance: 64 / 96 / 128 / 192 px) against the FP64 oracle, element by element.
+    Each stack's grid holds 288 parameter sets, so every segment ends in a ragged chunk (the
+    default chunks are 256 sets, 64 at 192 px).  Tolerance: 1e-3 plus the float32 output's rounding."""
+    bioem, ctx = env
+    cfg, wl, stacks, projsets, shifts = batch_case
+    batch = bioem.Batch(ctx, stacks, projsets, shifts)
+    got = batch.run().cpu().numpy().copy()
+    assert ctx.status() == 0
+    batch.close()
+    col = 0
+    for k, im in enumerate(stacks):
+        st = wl["stacks"][k]
+        sc = st["config"]
+        assert len(st["quats"]) * len(st["ctfs"]) % 64 != 0   # ragged last chunk
+        imgs = _stack_images(wl, k)
+        for m in range(cfg.n_models):
+            ref = oracle.score(imgs, wl["atoms"][m], st["quats"], st["ctfs"], sc.sigma_A, sc.pixel_A, sc.max_shift)
+            np.testing.assert_allclose(got[m, col:col + im.n_img], ref["logP"], rtol=3e-7, atol=TOL,
+                                       err_msg=f"model {m}, stack {k} ({sc.npix} px)")
+        col += im.n_img
+
+
 def test_autotune_and_cache(env, batch_case, tmp_path):
     bioem, ctx = env
     cfg, wl, stacks, projsets, shifts = batch_case
@@ -116,4 +141,14 @@ def test_autotune_and_cache(env, batch_case, tmp_path):
     batch = bioem.Batch(ctx, stacks, projsets, shifts)
     out = batch.run().cpu().numpy()
     assert np.all(np.isfinite(out))
+    os.remove(path)
+    # a corrupted cache: the invalid entry for this case is skipped, the case is tuned afresh and
+    # the file is rewritten with valid lines only
+    with open(path, "w") as f:
+        f.write(f"128 {shifts[2]} 5\n999 4 64\nnot a number\n")
+    chunk2 = bioem.autotune(ctx, stacks[2], projsets[0][2], shifts[2], path)
+    assert chunk2 in (pb * 2, pb * 8, pb * 32, pb * 64, pb * 128)
+    taken, skipped = bioem.autotune_load(path)
+    assert skipped == 0 and taken >= 1
+    assert f"128 {shifts[2]} {chunk2}" in open(path).read()
     os.remove(path)

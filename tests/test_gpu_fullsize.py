@@ -70,3 +70,67 @@ def test_full_size_sampled_orientations_match_oracle(full):
         assert abs(res["best_logL"][w] - b[4]) <= TOL
         if b[0] == 0:   # the oracle's best over the claimed orientation's PSFs and shifts
             assert (int(res["best_ctf"][w]), int(res["best_dy"][w]), int(res["best_dx"][w])) == tuple(b[1:4])
+
+
+def test_full_size_peak_neighbourhood_matches_oracle(full):
+    """8 images x 2048 parameter sets around the posterior peak: per image, its 64 grid orientations
+    nearest the true orientation plus 192 orientations shared by all eight, x all 8 PSFs.  The
+    per-orientation ln P of the full-size run (the benchmarked launch configuration) matches the
+    oracle at 1e-3 there, where rho is largest and the FP32 error budget is tightest."""
+    cfg, wl, imgs, logp, res = full
+    rng = np.random.default_rng(8 * 2048)
+    sel = rng.choice(2048, size=8, replace=False)
+    shared = np.sort(rng.choice(36864, size=192, replace=False))
+    ctfs = wl["ctfs"]
+    shared_projs = oracle.projections(wl["atoms"], wl["quats"][shared], ctfs, cfg.sigma_A, cfg.npix, cfg.pixel_A)
+    worst = 0.0
+    at_peak = 0
+    for w in sel:
+        truth = workloads.image_truth(cfg, int(w))
+        near = workloads.nearest_orientations(wl["quats"], truth["quat"], 64)
+        near = np.array([q for q in near if q not in set(shared)])
+        own = oracle.projections(wl["atoms"], wl["quats"][near], ctfs, cfg.sigma_A, cfg.npix, cfg.pixel_A)
+        qs = np.concatenate([near, shared])
+        r = oracle.score(imgs[w:w + 1], wl["atoms"], wl["quats"][qs], ctfs, cfg.sigma_A, cfg.pixel_A, cfg.max_shift,
+                         projs=np.concatenate([own, shared_projs]))
+        d = np.abs(res["logP_orient"][w, qs] - r["logP_orient"][0])
+        worst = max(worst, float(d.max()))
+        assert d.max() <= TOL, (w, int(qs[np.argmax(d)]), float(d.max()))
+        # does the neighbourhood hold the posterior peak (its best orientation beats the random ones)?
+        at_peak += int(r["logP_orient"][0, :len(near)].max() > r["logP_orient"][0, len(near):].max())
+    assert at_peak >= 6, at_peak   # the sets sample the peak for (nearly) every image
+    print(f"peak neighbourhood: max |dlogP_orient| = {worst:.2e}, peak inside for {at_peak} of 8 images")
+
+
+def test_full_size_random_pairs_max_loglik(full):
+    """max_d ln L on 1000 random (image, parameter set) pairs through bioem_score_pairs (the 2048
+    prepared images of the throughput workload against single parameter sets of the full grid),
+    against the oracle at 1e-3."""
+    import torch
+    import paper_1609_06634_gb300 as bioem
+    cfg, wl, imgs, logp, res = full
+    rng = np.random.default_rng(1000)
+    q_pool = np.sort(rng.choice(36864, size=125, replace=False))   # 125 orientations x 8 PSFs = 1000 sets
+    img_pool = rng.choice(2048, size=100, replace=False)
+    pair_img = img_pool[rng.integers(0, 100, size=1000)]            # set j is paired with image pair_img[j]
+    ctx = bioem.Context(0)
+    dev = torch.device("cuda", 0)
+    im = bioem.prepare_images(ctx, torch.from_numpy(imgs).to(dev), cfg.pixel_A)
+    ps = bioem.project_model(ctx, torch.from_numpy(wl["atoms"]).to(dev), cfg.sigma_A,
+                             torch.from_numpy(wl["quats"][q_pool]).to(dev), wl["ctfs"], cfg.npix, cfg.pixel_A)
+    got = np.empty(1000)
+    for j in range(1000):
+        pmax, _ = bioem.score_pairs(ctx, im, ps, cfg.max_shift, ps_begin=j, ps_count=1)
+        got[j] = pmax[int(pair_img[j]), 0].item()
+    assert ctx.status() == 0
+    projs = oracle.projections(wl["atoms"], wl["quats"][q_pool], wl["ctfs"], cfg.sigma_A, cfg.npix, cfg.pixel_A)
+    n = cfg.npix * cfg.npix
+    want = np.empty(1000)
+    for w in np.unique(pair_img):
+        js = np.nonzero(pair_img == w)[0]
+        p = projs[js].reshape(len(js), -1)
+        c_o, c_oo = oracle.moments(imgs[w])
+        c_co = oracle.correlation_all_shifts(imgs[w], projs[js], cfg.max_shift)
+        lnl = oracle.closed_form_loglik(c_o, c_oo, p.sum(axis=1)[:, None], (p * p).sum(axis=1)[:, None], c_co, n)
+        want[js] = lnl.max(axis=1)
+    np.testing.assert_allclose(got, want, rtol=0, atol=TOL)

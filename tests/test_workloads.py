@@ -130,3 +130,15 @@ def test_hopf_cell_and_children():
     np.testing.assert_array_equal(workloads.hopf_coarse_index(3, 1, kids), np.repeat(np.arange(576), 64).reshape(576, 64))
     # a fine point's cell at the coarse level is its parent
     np.testing.assert_array_equal(workloads.hopf_cell(1, fine), workloads.hopf_coarse_index(3, 1, np.arange(len(fine))))
+
+
+def test_nearest_orientations_brute_force():
+    """The k nearest grid quaternions by |<g, q>| (q and -q one orientation), closest first."""
+    rng = np.random.default_rng(12)
+    grid = workloads.random_quaternions(500, rng)
+    q = -grid[17] * 0.999 + 0.001 * rng.standard_normal(4)
+    q /= np.linalg.norm(q)
+    idx = workloads.nearest_orientations(grid, q, 10)
+    assert idx[0] == 17
+    d = np.abs(grid @ q)
+    np.testing.assert_array_equal(idx, np.argsort(-d, kind="stable")[:10])

@@ -35,6 +35,34 @@ def _noalloc(bioem, ctx, im, ps, max_shift, out):
     return bioem.lib().bioem_score_noalloc(ctx._h, im._h, ps._h, int(max_shift), ctypes.c_void_p(out.data_ptr()))
 
 
+def test_noalloc_first_on_a_fresh_context_allocates_nothing(env):
+    """On a new context, before any other scoring call: after one warm-up call (which loads the
+    kernels' code), a further call leaves the device's free memory unchanged, and both results
+    equal bioem_score's, which runs afterwards on the same context."""
+    import torch
+    bioem, _ = env
+    ctx = bioem.Context(0)
+    cfg = workloads.get_config("tiny")
+    wl = workloads.workload(cfg, n_img=8)
+    dev = torch.device("cuda", 0)
+    im = bioem.prepare_images(ctx, torch.from_numpy(oracle.synthesize_images(wl)).to(dev), cfg.pixel_A)
+    ps = bioem.project_model(ctx, torch.from_numpy(wl["atoms"]).to(dev), cfg.sigma_A,
+                             torch.from_numpy(wl["quats"]).to(dev), wl["ctfs"], cfg.npix, cfg.pixel_A)
+    out1 = torch.full((8,), float("nan"), dtype=torch.float64, device=dev)
+    out2 = torch.full((8,), float("nan"), dtype=torch.float64, device=dev)
+    assert _noalloc(bioem, ctx, im, ps, cfg.max_shift, out1) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info(dev)
+    assert _noalloc(bioem, ctx, im, ps, cfg.max_shift, out2) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info(dev)
+    assert free1 == free0
+    assert ctx.status() == 0
+    want = bioem.score(ctx, im, ps, cfg.max_shift).cpu().numpy()
+    np.testing.assert_allclose(out1.cpu().numpy(), want, rtol=0, atol=TOL)
+    np.testing.assert_allclose(out2.cpu().numpy(), want, rtol=0, atol=TOL)
+
+
 def test_noalloc_matches_score_twice(env):
     import torch
     bioem, ctx = env

@@ -27,6 +27,7 @@ from .generate import (  # noqa: F401
     hopf_grid,
     hopf_coarse_index,
     image_truth,
+    nearest_orientations,
     random_quaternions,
     standard_normal_noise,
     workload,

@@ -179,6 +179,14 @@ def hopf_coarse_index(fine_level: int, coarse_level: int, fine_index: np.ndarray
     return (pix >> (2 * d)) * n_psi_c + (k >> d)
 
 
+def nearest_orientations(grid: np.ndarray, q: np.ndarray, k: int) -> np.ndarray:
+    """Indices of the k grid quaternions closest to q (largest |<g, q>|: q and -q are one
+    orientation), closest first.  Picks the "truth neighbourhood" of a synthetic image on a grid."""
+    dots = np.abs(np.asarray(grid, dtype=np.float64) @ np.asarray(q, dtype=np.float64))
+    idx = np.argpartition(-dots, k - 1)[:k]
+    return idx[np.argsort(-dots[idx], kind="stable")]
+
+
 def defocus_grid(n: int, lo_um: float, hi_um: float) -> np.ndarray:
     """n defocus values (A), evenly spaced over [lo, hi] um, endpoints included."""
     return np.linspace(lo_um, hi_um, n) * 1.0e4
