@@ -39,16 +39,43 @@ sys.path.insert(0, ROOT)
 import workloads  # noqa: E402
 
 METRIC = "parameter-set×image evals/sec (all shifts) at stated |Δlog P| vs FP64 oracle"
+# The scoring form the throughput line reports (both hold |d log P| <= 1e-3 at the posterior peak).
+HEADLINE_PRECISION = "fp32"
 UNIT = "evals/s"
-SCORE_SRC = os.path.join(ROOT, "paper_1609_06634_gb300", "csrc", "score.cu")
+CSRC = os.path.join(ROOT, "paper_1609_06634_gb300", "csrc")
 
-# DRAM bytes per launch of k_score_gemm on the precision workloads (64 images x 6912 sets, +-4 px), mean
-# of the one-pass captures of each form's launches, valid only for the gemm.cu source they were taken on.
-K_SCORE_GEMM_TRAFFIC = {"source_sha256": "c077eb2210d57e6d059a1b04ea3fb72797d3c8258f89dab99d405be3b32075f2", "bytes_per_launch": {'128/bf16x2': 3794691556, '128/fp16x2': 5033599431, '128/bf16x2_real': 4005294820, '128/fp16x2_real': 5370143033, '64/bf16x2': 895775374, '64/fp16x2': 896910507, '64/bf16x2_real': 868407154, '64/fp16x2_real': 869934222}}
-# DRAM traffic of k_score from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass,
-# of one full-size launch of this workload: 87,376 parameter sets x 2048 images, 29.35 GB + 2.20 GB),
-# valid only for the kernel source it was taken on; bytes per evaluated pair.
-K_SCORE_TRAFFIC = {"source_sha256": "cba5213eed8b33ca5d746cadb8c67af3cb4df22ceb85fda66eee095b05bf436e", "bytes_per_pair": (29.352918e9 + 2.202553e9) / (87376 * 2048)}
+# Identity of a kernel's source: the sha256 of the text between two markers of its file (plus any
+# shared header it includes), so a stored DRAM figure stays valid while that kernel is unchanged.
+KERNEL_SOURCES = {
+    "k_score": (os.path.join(CSRC, "score.cu"), "template <int N_, int SMAX_",
+                "// ---------------------------------------------------------------------------- reductions (float64)",
+                []),
+    "k_score_gemm": (os.path.join(CSRC, "gemm.cu"), "struct GemmArgs {", "bool mode_fp16(int mode)",
+                     [os.path.join(CSRC, "tc_util.cuh")]),
+    "k_score_tc": (os.path.join(CSRC, "score_tc.cu"), "namespace tcs {", "int bioem_tc_supported(",
+                   [os.path.join(CSRC, "tc_util.cuh")]),
+}
+
+
+def kernel_source_sha(kernel: str) -> str:
+    path, begin, end, extra = KERNEL_SOURCES[kernel]
+    txt = open(path).read()
+    h = hashlib.sha256(txt[txt.index(begin):txt.index(end)].encode())
+    for e in extra:
+        h.update(open(e, "rb").read())
+    return h.hexdigest()
+
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one-pass ncu captures), valid only for
+# the kernel source they were taken on (kernel_source_sha).
+#   k_score: per evaluated pair, from one launch of 2048 images x 4608 sets (above L2), scaled by
+#            pairs to the bench's launches (profiles/k_score_throughput.md).
+#   k_score_gemm: per launch of the precision workloads (64 images x 6912 sets, +-4 px).
+K_SCORE_TRAFFIC = {"source_sha256": "f7c59412dc327757fa81aa0019b32c26097be974ce46c6738e7d371a235d31c7", "bytes_per_pair": (1558311424 + 117285632) / (2048 * 4608)}
+K_SCORE_GEMM_TRAFFIC = {"source_sha256": "", "bytes_per_launch": {
+    '128/bf16x2': 3794691556, '128/fp16x2': 5033599431, '128/bf16x2_real': 4005294820, '128/fp16x2_real': 5370143033,
+    '64/bf16x2': 895775374, '64/fp16x2': 896910507, '64/bf16x2_real': 868407154, '64/fp16x2_real': 869934222}}
+K_SCORE_TC_TRAFFIC = {"source_sha256": "", "bytes_per_pair": None}
 
 
 def parse_args():
@@ -65,6 +92,10 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--epochs", type=int, default=16, help="proposal workload: training epochs")
+    ap.add_argument("--precision", default=None,
+                    help="throughput workload: scoring form (fp32: pruned FFT on CUDA cores; fp16x2_fft: its "
+                         "column transforms as split-FP16 tensor-core products); default: the form the bench "
+                         "reports as its headline")
     return ap.parse_args()
 
 
@@ -299,6 +330,7 @@ def bench_ours(args):
     n_ps = len(quats_np) * len(ctfs)
 
     ctx = bioem.Context(local)
+    precision = args.precision or HEADLINE_PRECISION
     atoms_d = torch.from_numpy(wl["atoms"]).to(dev)
     quats_d = torch.from_numpy(np.ascontiguousarray(quats_np)).to(dev)
     images_d = synth_images(bioem, ctx, cfg, atoms_d, rank * n_img, n_img)
@@ -318,6 +350,8 @@ def bench_ours(args):
         if world > 1:
             tdist.barrier()
 
+    ctx.set_precision(precision)
+    score_kernel = "k_score_tc" if precision == "fp16x2_fft" else "k_score"
     for _ in range(args.warmup):
         step(images_d, atoms_d, quats_d)
     torch.cuda.synchronize()
@@ -346,9 +380,9 @@ def bench_ours(args):
     barrier()
     ms = ev0.elapsed_time(ev1)
     launches = ctx.launch_count()
-    k_ms, k_n = ctx.kernel_time("k_score")
+    k_ms, k_n = ctx.kernel_time(score_kernel)
     kernel_ms = {name: ctx.kernel_time(name)[0] for name in
-                 ("k_prepare_images", "k_ctf_table", "k_project", "k_psf_spectra", "k_score", "k_reduce_wave",
+                 ("k_prepare_images", "k_ctf_table", "k_project", "k_psf_spectra", score_kernel, "k_reduce_wave",
                   "k_finalize")}
     ctx.set_kernel_timing(False)
     if ctx.status() != 0:
@@ -404,12 +438,12 @@ def bench_ours(args):
             pass
         nominal = props.multi_processor_count * 128 * 2 * peak_mhz * 1e6 / 1e12
         peak = peaks["fp32_tflops"]
-        sha = hashlib.sha256(open(SCORE_SRC, "rb").read()).hexdigest()
         traffic = None
-        if K_SCORE_TRAFFIC["source_sha256"] == sha and K_SCORE_TRAFFIC["bytes_per_pair"]:
-            traffic = K_SCORE_TRAFFIC["bytes_per_pair"] * n_img * n_ps / max(1, k_n / args.steps)
+        table = K_SCORE_TC_TRAFFIC if score_kernel == "k_score_tc" else K_SCORE_TRAFFIC
+        if table["source_sha256"] == kernel_source_sha(score_kernel) and table["bytes_per_pair"]:
+            traffic = table["bytes_per_pair"] * n_img * n_ps / max(1, k_n / args.steps)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "k_score",
+                "traffic": traffic, "kernel": score_kernel,
                 "peak_basis": (f"measured: FP32 multiply-add microbenchmark (bioem_fma_peak, {peaks['fp32_form']}) "
                                f"on this GPU in this run, median SM clock {peaks['sm_mhz']} MHz during it"),
                 "peak_nominal": nominal,
@@ -419,9 +453,23 @@ def bench_ours(args):
         if clk and clk.get("sm_mhz") and peaks.get("sm_mhz"):
             # the peak rescaled from the microbenchmark's clock to the clock seen in the timed steps
             roof["frac_at_observed_clock"] = achieved / (peak * clk["sm_mhz"] / peaks["sm_mhz"])
+        if score_kernel == "k_score_tc":
+            # the column transforms' tensor-core products: per pair 2 MMA terms x 128 rows x 64 columns
+            # x 256 K x 2 flop = 8.39 Mflop, against the measured dense 16-bit rate (FP16 = BF16 rate)
+            tflop = 2 * 128 * 64 * 256 * 2 * n_img * n_ps * args.steps / (k_ms / 1e3) / 1e12
+            bf16 = None
+            try:
+                bf16 = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("bf16_tflops")
+            except (OSError, ValueError):
+                pass
+            roof["tensor"] = {"achieved": tflop, "peak": bf16 or 1900.0, "unit": "TFLOP/s",
+                              "frac": tflop / (bf16 or 1900.0),
+                              "peak_basis": "measured" if bf16 else "fallback",
+                              "work": "stage-A products, 8.39 Mflop per pair (two split terms, stacked hi/lo rows)"}
+        dtype = "f32 (column transforms: fp16x2 tensor cores)" if precision == "fp16x2_fft" else "f32"
         result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                   "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-                  "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                  "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic", "precision": precision,
                   "config": workload_config(cfg, n_img, n_ps), "roofline": roof, "e2e": e2e,
                   "gpu_launches": int(launches), "clocks": clk,
                   "kernel_ms_per_step": {k: v / args.steps for k, v in kernel_ms.items()}}
@@ -751,8 +799,7 @@ def bench_precision(args):
                     executed = 6.0 * K * (-(-n_ps // 128) * 128) * (-(-n_img // ipt) * 256)
                     per_launch_ms = k_ms / max(1, k_n)
                     achieved = alg / max(1, k_n / args.steps) / (per_launch_ms / 1e3) / 1e12
-                    gsha = hashlib.sha256(open(os.path.join(ROOT, "paper_1609_06634_gb300", "csrc", "gemm.cu"),
-                                                "rb").read()).hexdigest()
+                    gsha = kernel_source_sha("k_score_gemm")
                     traffic = (K_SCORE_GEMM_TRAFFIC["bytes_per_launch"].get(f"{cfg.npix}/{mode}")
                                if K_SCORE_GEMM_TRAFFIC["source_sha256"] == gsha and n_img == 64 and n_ps == 6912 else None)
                     f["roofline"] = {"bound": "tensor", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",

@@ -88,6 +88,13 @@ int bioem_set_scratch_limit(bioem_ctx* ctx, unsigned long long bytes);
  * zero-mean, unit-norm image, instead of the 2 N (N/2 + 1) half-spectrum terms. */
 #define BIOEM_PRECISION_BF16X2_REAL 3
 #define BIOEM_PRECISION_FP16X2_REAL 4
+/* The FP32 form (the pruned two-stage inverse transform of the Fourier product, Sec. 3.3) with its
+ * first stage, the ky transform of every column restricted to the displacement window, run as a
+ * split-precision matrix product on the tensor cores: FP16 hi + lo parts of both the transform
+ * matrix and the products (all four cross terms), FP32 accumulation; the products, the kx stage,
+ * the likelihood and everything after it as in the FP32 form.  128 px images, max_shift <= 16
+ * only (UNSUPPORTED_SIZE otherwise); no operand copies are kept. */
+#define BIOEM_PRECISION_FP16X2_FFT 5
 int bioem_set_precision(bioem_ctx* ctx, int mode);
 int bioem_get_precision(const bioem_ctx* ctx);
 
@@ -337,7 +344,8 @@ int bioem_fma_peak(bioem_ctx* ctx, int kind, int reps, double* flops_per_s);
  * context's stream around every launch; bioem_kernel_time synchronises the stream and returns the
  * summed device time (ms) and the launch count of one kernel, by name: "k_prepare_images",
  * "k_project", "k_ctf_table", "k_psf_spectra", "k_psf_real", "k_score", "k_reduce_wave",
- * "k_finalize", "k_pairs_out", "k_gemm_ops", "k_score_gemm", "k_ensemble", "k_lse_merge".
+ * "k_finalize", "k_pairs_out", "k_gemm_ops", "k_score_gemm", "k_ensemble", "k_lse_merge",
+ * "k_score_tc".
  * bioem_reset_kernel_stats
  * zeroes both. */
 int bioem_set_kernel_timing(bioem_ctx* ctx, int enable);

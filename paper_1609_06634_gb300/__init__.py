@@ -89,13 +89,14 @@ class Context:
     def set_scratch_limit(self, nbytes: int):
         _check(self, lib().bioem_set_scratch_limit(self._h, int(nbytes)), "set_scratch_limit")
 
-    PRECISIONS = {"fp32": 0, "bf16x2": 1, "fp16x2": 2, "bf16x2_real": 3, "fp16x2_real": 4}
+    PRECISIONS = {"fp32": 0, "bf16x2": 1, "fp16x2": 2, "bf16x2_real": 3, "fp16x2_real": 4, "fp16x2_fft": 5}
 
     def set_precision(self, mode):
         """Arithmetic of the correlation step for score/score_all/best_params/score_pairs: "fp32"
         (FFT form on the CUDA cores), "bf16x2" or "fp16x2" (two-term split-precision GEMM on the
         tensor cores over the half spectrum), "bf16x2_real" / "fp16x2_real" (the same GEMM over
-        real-space pixels), or the C constant."""
+        real-space pixels), "fp16x2_fft" (the FFT form with its column transforms as split-FP16
+        tensor-core products; 128 px, max_shift <= 16), or the C constant."""
         m = self.PRECISIONS[mode] if isinstance(mode, str) else int(mode)
         _check(self, lib().bioem_set_precision(self._h, m), "set_precision")
 

@@ -16,8 +16,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libbioem_gb300.so")
-SOURCES = ["abi.cu", "prep_project.cu", "score.cu", "cnn.cu", "gemm.cu", "ensemble.cu", "peak.cu"]
-HEADERS = [os.path.join(CSRC, "bioem_internal.cuh"), os.path.join(ROOT, "include", "bioem.h")]
+SOURCES = ["abi.cu", "prep_project.cu", "score.cu", "cnn.cu", "gemm.cu", "ensemble.cu", "peak.cu", "score_tc.cu"]
+HEADERS = [os.path.join(CSRC, "bioem_internal.cuh"), os.path.join(CSRC, "tc_util.cuh"),
+           os.path.join(ROOT, "include", "bioem.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC,-O2",
          "-I" + os.path.join(ROOT, "include")]

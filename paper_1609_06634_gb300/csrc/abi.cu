@@ -28,7 +28,7 @@ int bioem_check_cuda(bioem_ctx* ctx, cudaError_t e, const char* what) {
 const char* const bioem_kernel_names[KID_COUNT] = {
     "k_prepare_images", "k_project", "k_ctf_table", "k_psf_spectra", "k_psf_real",
     "k_score", "k_reduce_wave", "k_finalize", "k_pairs_out", "k_gemm_ops", "k_score_gemm", "k_ensemble",
-    "k_lse_merge"};
+    "k_lse_merge", "k_score_tc"};
 
 void bioem_launch_begin(bioem_ctx* ctx, int kid) {
     if (!ctx->timing) return;
@@ -199,7 +199,7 @@ void bioem_destroy(bioem_ctx* ctx) {
 
 int bioem_set_precision(bioem_ctx* ctx, int mode) {
     if (!ctx) return BIOEM_ERR_INVALID_ARG;
-    if (mode < BIOEM_PRECISION_FP32 || mode > BIOEM_PRECISION_FP16X2_REAL)
+    if (mode < BIOEM_PRECISION_FP32 || mode > BIOEM_PRECISION_FP16X2_FFT)
         return bioem_set_error(ctx, BIOEM_ERR_INVALID_ARG, "unknown precision mode %d", mode);
     ctx->precision = mode;
     return BIOEM_OK;
@@ -331,9 +331,12 @@ static int check_pair(bioem_ctx* ctx, const bioem_images* im, const bioem_projse
     if (im->nx != ps->nx || im->ny != ps->ny || fabs(im->pixel_A - ps->pixel_A) > 1e-9 * im->pixel_A)
         return bioem_set_error(ctx, BIOEM_ERR_INVALID_ARG, "images and projections differ in size or pixel");
     if (max_shift < 0) return bioem_set_error(ctx, BIOEM_ERR_INVALID_ARG, "negative max_shift");
-    if (ctx->precision == BIOEM_PRECISION_FP32 ? !bioem_score_supported(im->nx, max_shift)
-                                               : !bioem_gemm_supported(im->nx, max_shift))
-        return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE, "max_shift %d unsupported at %d px", max_shift, im->nx);
+    const int supported = ctx->precision == BIOEM_PRECISION_FP32       ? bioem_score_supported(im->nx, max_shift)
+                          : ctx->precision == BIOEM_PRECISION_FP16X2_FFT ? bioem_tc_supported(im->nx, max_shift)
+                                                                         : bioem_gemm_supported(im->nx, max_shift);
+    if (!supported)
+        return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE, "max_shift %d unsupported at %d px in precision mode %d",
+                               max_shift, im->nx, ctx->precision);
     if (ps->n_ps == 0) return bioem_set_error(ctx, BIOEM_ERR_INVALID_ARG, "empty parameter set");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return bioem_set_error(ctx, BIOEM_ERR_CUDA, "cudaSetDevice");
     return BIOEM_OK;

@@ -11,7 +11,8 @@
 // ------------------------------------------------------------------ kernel accounting
 enum bioem_kernel_id {
     KID_PREPARE = 0, KID_PROJECT, KID_CTF_TABLE, KID_PSF_SPECTRA, KID_PSF_REAL, KID_SCORE, KID_REDUCE_WAVE,
-    KID_FINALIZE, KID_PAIRS_OUT, KID_GEMM_OPS, KID_SCORE_GEMM, KID_ENSEMBLE, KID_LSE_MERGE, KID_COUNT
+    KID_FINALIZE, KID_PAIRS_OUT, KID_GEMM_OPS, KID_SCORE_GEMM, KID_ENSEMBLE, KID_LSE_MERGE, KID_SCORE_TC,
+    KID_COUNT
 };
 extern const char* const bioem_kernel_names[KID_COUNT];
 
@@ -147,6 +148,11 @@ int bioem_gemm_prepare(bioem_ctx* ctx, const bioem_images* im, const bioem_projs
 int bioem_gemm_records(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, int max_shift, int mode,
                        int ps_lo, int ps_hi, float* rec_t, float* rec_s, int* rec_d);
 void bioem_gemm_cache_free(bioem_gemm_cache* c, cudaStream_t stream);
+
+// score_tc.cu (FP32 scoring form with its column transforms as split-FP16 tensor-core products)
+int bioem_tc_supported(int npix, int max_shift);
+int bioem_tc_records(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, int max_shift, int wbegin,
+                     int wl, float* rec_t, float* rec_s, int* rec_d);
 
 // abi.cu
 void bioem_launch_begin(bioem_ctx* ctx, int kid);   // call before a kernel launch

@@ -824,6 +824,16 @@ int bioem_score_supported(int npix, int max_shift) {
 
 int bioem_launch_score(bioem_ctx* ctx, const bioem_images* im, const bioem_projset* ps, int max_shift,
                        const bioem_score_out& out) {
+    if (ctx->precision == BIOEM_PRECISION_FP16X2_FFT) {
+        if (!bioem_tc_supported(im->nx, max_shift))
+            return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE,
+                                   "tensor-core column transforms: 128 px and max_shift <= 16 only (%d px, %d)",
+                                   im->nx, max_shift);
+        auto records = [&](int wbegin, int wl, float* rec_t, float* rec_s, int* rec_d) -> int {
+            return bioem_tc_records(ctx, im, ps, max_shift, wbegin, wl, rec_t, rec_s, rec_d);
+        };
+        return run_waves(ctx, im, ps, max_shift, 16, ps->nctf, out, records);
+    }
     if (ctx->precision != BIOEM_PRECISION_FP32) {
         if (!bioem_gemm_supported(im->nx, max_shift))
             return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE,

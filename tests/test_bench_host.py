@@ -50,9 +50,13 @@ def test_every_global_name_in_bench_is_defined():
 
 def test_traffic_tables_and_work_per_eval():
     bench = _bench()
+    # a stored figure names the kernel source it was taken on ("" until one is taken)
+    for k in ("k_score", "k_score_gemm", "k_score_tc"):
+        assert len(bench.kernel_source_sha(k)) == 64
     assert len(bench.K_SCORE_TRAFFIC["source_sha256"]) == 64 and bench.K_SCORE_TRAFFIC["bytes_per_pair"] > 0
     t = bench.K_SCORE_GEMM_TRAFFIC
-    assert len(t["source_sha256"]) == 64
+    assert len(t["source_sha256"]) in (0, 64)
+    assert len(bench.K_SCORE_TC_TRAFFIC["source_sha256"]) in (0, 64)
     assert set(t["bytes_per_launch"]) == {f"{n}/{m}" for n in (128, 64)
                                           for m in ("bf16x2", "fp16x2", "bf16x2_real", "fp16x2_real")}
     # 6 H + 2.5 n log2 n + 4 S at 128 px, S = 1089: 0.628 Mflop
