@@ -98,6 +98,17 @@ int bioem_set_scratch_limit(bioem_ctx* ctx, unsigned long long bytes);
 int bioem_set_precision(bioem_ctx* ctx, int mode);
 int bioem_get_precision(const bioem_ctx* ctx);
 
+/* Failure-detection test hook (no counterpart in the paper).  Arms the next tensor-core scoring
+ * launch of this context (precision BF16X2 / FP16X2 / *_REAL or FP16X2_FFT) to leave K chunk
+ * skip_chunk of every block unfed: in the split-precision GEMM the producer issues no copies for
+ * it, in the FP16X2_FFT form no MMAs and no commit, so the barrier that chunk's consumers wait on
+ * never completes.  Every barrier wait of that launch gives up after wait_ns (1 us .. 2 s) instead
+ * of the default 2 s; the kernel then raises BIOEM_ERR_TIMEOUT in the device status word, leaves its
+ * loops together, waits (bounded) for the copies and MMAs it did issue, frees its tensor memory and
+ * returns, and the context stays usable.  The scoring call's outputs are undefined.  One launch
+ * only; skip_chunk = -1 disarms.  Errors: INVALID_ARG. */
+int bioem_set_wait_test(bioem_ctx* ctx, long long skip_chunk, unsigned long long wait_ns);
+
 /* Free the context and everything it owns (not the handles made with it). */
 void bioem_destroy(bioem_ctx* ctx);
 

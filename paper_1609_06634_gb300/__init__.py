@@ -105,6 +105,11 @@ class Context:
         m = int(lib().bioem_get_precision(self._h))
         return {v: k for k, v in self.PRECISIONS.items()}[m]
 
+    def set_wait_test(self, skip_chunk: int, wait_ns: int = 5_000_000):
+        """bioem_set_wait_test: the next tensor-core scoring launch leaves K chunk skip_chunk unfed, so a
+        bounded barrier wait (wait_ns) expires and the launch ends with BIOEM_ERR_TIMEOUT in the status."""
+        _check(self, lib().bioem_set_wait_test(self._h, int(skip_chunk), int(wait_ns)), "set_wait_test")
+
     def set_kernel_timing(self, on: bool = True):
         """Record CUDA events on this context's stream around every library kernel launch."""
         _check(self, lib().bioem_set_kernel_timing(self._h, 1 if on else 0), "set_kernel_timing")

@@ -23,6 +23,7 @@ SIGNATURES = {
     "bioem_set_scratch_limit": (c_int, [c_void_p, c_ull]),
     "bioem_set_precision": (c_int, [c_void_p, c_int]),
     "bioem_get_precision": (c_int, [c_void_p]),
+    "bioem_set_wait_test": (c_int, [c_void_p, ctypes.c_longlong, c_ull]),
     "bioem_destroy": (None, [c_void_p]),
     "bioem_get_status": (c_int, [c_void_p, ctypes.POINTER(c_int)]),
     "bioem_last_error": (c_char_p, [c_void_p]),

@@ -127,6 +127,7 @@ int bioem_create(bioem_ctx** out, int device, void* cuda_stream) {
     ctx->device = device;
     ctx->stream = (cudaStream_t)cuda_stream;
     ctx->scratch_limit = 2ull << 30;
+    ctx->test_skip_chunk = -1;
     int rc = BIOEM_OK;
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
@@ -206,6 +207,14 @@ int bioem_set_precision(bioem_ctx* ctx, int mode) {
 }
 
 int bioem_get_precision(const bioem_ctx* ctx) { return ctx ? ctx->precision : BIOEM_ERR_INVALID_ARG; }
+
+int bioem_set_wait_test(bioem_ctx* ctx, long long skip_chunk, unsigned long long wait_ns) {
+    if (!ctx || skip_chunk < -1 || (skip_chunk >= 0 && (wait_ns < 1000ull || wait_ns > 2000000000ull)))
+        return BIOEM_ERR_INVALID_ARG;
+    ctx->test_skip_chunk = skip_chunk;
+    ctx->test_wait_ns = skip_chunk >= 0 ? wait_ns : 0;
+    return BIOEM_OK;
+}
 
 int bioem_set_kernel_timing(bioem_ctx* ctx, int enable) {
     if (!ctx) return BIOEM_ERR_INVALID_ARG;

@@ -45,6 +45,9 @@ struct bioem_ctx {
     std::vector<bioem_timed_launch> pending;
     double kid_ms[KID_COUNT];
     int precision;   // BIOEM_PRECISION_*: the form bioem_score and its relatives use
+    // failure-detection test hook, armed for the next tensor-core scoring launch only
+    long long test_skip_chunk;            // -1: none
+    unsigned long long test_wait_ns;      // 0: the default limit
 };
 
 // Operands of the split-precision GEMM scoring form, built from a handle's spectra on first use

@@ -244,6 +244,8 @@ struct GemmArgs {
     int ps_lo, ps_hi;             // records for parameter sets [ps_lo, ps_hi)
     float c1;                     // (3 - n) / 2
     uint32_t idesc;
+    long long skip_chunk;         // failure-detection test: the producer skips this chunk's copies (-1: none)
+    unsigned long long wait_ns;   // limit of every barrier wait
     float* rec_t;                 // [n_img][ps_hi - ps_lo]
     float* rec_s;
     int* rec_d;
@@ -344,10 +346,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_score_gemm(const GemmArgs g
             bool ok = true;
             for (int ch = 0; ch < g.n_chunks; ++ch, ++it) {
                 const uint32_t s = it % NSTAGE, round = it / NSTAGE;
-                if (round > 0 && !mbar_wait(smem_u32(&bar_empty[s]), (round - 1) & 1, abort_v, g.status)) {
+                if (round > 0 && !mbar_wait(smem_u32(&bar_empty[s]), (round - 1) & 1, abort_v, g.status, g.wait_ns)) {
                     ok = false;
                     break;
                 }
+                if ((long long)it == g.skip_chunk) continue;   // test: this stage's barrier never completes
                 const uint32_t full = smem_u32(&bar_full[s]);
                 mbar_expect_tx(full, STAGE);
                 bulk_g2s(sbase + s * STAGE, ga + (size_t)ch * (2 * A_TERM), 2 * A_TERM, full);
@@ -358,7 +361,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_score_gemm(const GemmArgs g
         // copies still landing must not outlive the block: wait for the last phases issued
         for (uint32_t k = 1; k <= NSTAGE && k <= it; ++k) {
             const uint32_t i = it - k;
-            mbar_drain(smem_u32(&bar_full[i % NSTAGE]), (i / NSTAGE) & 1);
+            if ((long long)i == g.skip_chunk) continue;
+            mbar_drain(smem_u32(&bar_full[i % NSTAGE]), (i / NSTAGE) & 1, g.wait_ns);
         }
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issue: each group of GROUP chunks into a fresh accumulator buffer
@@ -368,7 +372,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_score_gemm(const GemmArgs g
         for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
             for (int gr = 0; gr < n_groups && ok; ++gr, ++gi) {
                 const uint32_t b = gi & 1, use = gi >> 1;
-                if (use > 0 && !mbar_wait(smem_u32(&bar_tempty[b]), (use - 1) & 1, abort_v, g.status)) {
+                if (use > 0 && !mbar_wait(smem_u32(&bar_tempty[b]), (use - 1) & 1, abort_v, g.status, g.wait_ns)) {
                     ok = false;
                     break;
                 }
@@ -377,7 +381,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_score_gemm(const GemmArgs g
                 const int ch1 = min(g.n_chunks, (gr + 1) * GROUP);
                 for (int ch = gr * GROUP; ch < ch1; ++ch, ++it) {
                     const uint32_t s = it % NSTAGE, round = it / NSTAGE;
-                    if (!mbar_wait(smem_u32(&bar_full[s]), round & 1, abort_v, g.status)) {
+                    if (!mbar_wait(smem_u32(&bar_full[s]), round & 1, abort_v, g.status, g.wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -401,7 +405,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_score_gemm(const GemmArgs g
         }
         // every MMA issued has completed before the block releases tensor memory
         umma_commit(smem_u32(&bar_drain));
-        mbar_drain(smem_u32(&bar_drain), 0);
+        mbar_drain(smem_u32(&bar_drain), 0, g.wait_ns);
     } else if (warp >= 2) {
         // ---------------- epilogue: two threads per parameset (tensor-memory lane), 128 columns each
         const int e = warp - 2;
@@ -423,7 +427,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_score_gemm(const GemmArgs g
             bool fail = false;
             for (int gr = 0; gr < n_groups; ++gr, ++gi) {
                 const uint32_t b = gi & 1, use = gi >> 1;
-                if (!fail) fail = !warp_all(mbar_wait(smem_u32(&bar_tfull[b]), use & 1, abort_v, g.status));
+                if (!fail) fail = !warp_all(mbar_wait(smem_u32(&bar_tfull[b]), use & 1, abort_v, g.status, g.wait_ns));
                 if (fail) continue;
                 tc_fence_after();
 #pragma unroll
@@ -686,6 +690,10 @@ int bioem_gemm_records(bioem_ctx* ctx, const bioem_images* im, const bioem_projs
     g.rec_s = rec_s;
     g.rec_d = rec_d;
     g.status = ctx->d_status;
+    g.skip_chunk = ctx->test_skip_chunk;
+    g.wait_ns = ctx->test_wait_ns ? ctx->test_wait_ns : kWaitNs;
+    ctx->test_skip_chunk = -1;   // armed for one launch
+    ctx->test_wait_ns = 0;
     const long long n_tiles = (long long)g.n_ptiles * g.n_itiles;
     if (n_tiles > 0x7fffffffll) return bioem_set_error(ctx, BIOEM_ERR_UNSUPPORTED_SIZE, "too many GEMM tiles");
     if (cudaFuncSetAttribute(k_score_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM) != cudaSuccess)

@@ -83,6 +83,8 @@ struct TcArgs {
     int* rec_d;
     int* status;
     int* work;
+    long long skip_chunk;         // failure-detection test: thread 0 skips this chunk's MMAs (-1: none)
+    unsigned long long wait_ns;   // limit of every barrier wait
 };
 
 struct TPart {
@@ -194,12 +196,12 @@ __device__ __forceinline__ bool block_any(bool f) { return __syncthreads_or(f ? 
 __device__ __forceinline__ void proxy_fence_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // Bounded wait on an mbarrier phase by any number of threads (false on expiry; raises the status bit).
-__device__ __forceinline__ bool bwait(uint32_t bar, uint32_t parity, int* status) {
+__device__ __forceinline__ bool bwait(uint32_t bar, uint32_t parity, int* status, unsigned long long limit_ns) {
     if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
     for (;;) {
         if (mbar_try(bar, parity)) return true;
-        if (globaltimer() - t0 > kWaitNs) {
+        if (globaltimer() - t0 > limit_ns) {
             atomicOr(status, BIOEM_DEV_TIMEOUT);
             return false;
         }
@@ -355,7 +357,7 @@ __global__ void __launch_bounds__(tcs::THREADS, 1) k_score_tc(const TcArgs g) {
                 for (int c = 0; c < KCH; ++c, ++cc) {
                     const uint32_t s = cc & 1;
                     bool ok = true;
-                    if (cc >= 2) ok = bwait(smem_u32(&bar_empty[s]), ((cc >> 1) - 1) & 1, g.status);
+                    if (cc >= 2) ok = bwait(smem_u32(&bar_empty[s]), ((cc >> 1) - 1) & 1, g.status, g.wait_ns);
                     if (ok) {
                         const int ky0 = 16 * c + 4 * kg;
                         float2 o[4];
@@ -392,7 +394,7 @@ __global__ void __launch_bounds__(tcs::THREADS, 1) k_score_tc(const TcArgs g) {
                         fail = true;
                         break;
                     }
-                    if (tid == 0) {
+                    if (tid == 0 && (long long)cc != g.skip_chunk) {   // test: skipped chunk, no commit
                         tc_fence_after();
                         const uint32_t d = tmem + buf * 256;
                         const uint32_t a0 = sbase + (uint32_t)OFF_E + c * A_CHUNK;
@@ -434,7 +436,7 @@ __global__ void __launch_bounds__(tcs::THREADS, 1) k_score_tc(const TcArgs g) {
             const uint32_t eg = gg - 1 - (gi < n_groups ? 1 : 0);   // its group number
             const uint32_t eb = eg & 1;
             const int ep0 = lo + (gi - 1) * PG;
-            const bool ok = bwait(smem_u32(&bar_tfull[eb]), (eg >> 1) & 1, g.status);
+            const bool ok = bwait(smem_u32(&bar_tfull[eb]), (eg >> 1) & 1, g.status, g.wait_ns);
             tc_fence_after();
             float qv[32];
             {
@@ -568,7 +570,7 @@ __global__ void __launch_bounds__(tcs::THREADS, 1) k_score_tc(const TcArgs g) {
     // ---------------- teardown: every MMA issued has completed before tensor memory is released
     if (tid == 0) {
         umma_commit(smem_u32(&bar_drain));
-        mbar_drain(smem_u32(&bar_drain), 0);
+        mbar_drain(smem_u32(&bar_drain), 0, g.wait_ns);
     }
     tc_fence_before();
     __syncthreads();
@@ -614,6 +616,10 @@ int bioem_tc_records(bioem_ctx* ctx, const bioem_images* im, const bioem_projset
     a.rec_d = rec_d;
     a.status = ctx->d_status;
     a.work = ctx->d_work;
+    a.skip_chunk = ctx->test_skip_chunk;
+    a.wait_ns = ctx->test_wait_ns ? ctx->test_wait_ns : kWaitNs;
+    ctx->test_skip_chunk = -1;   // armed for one launch
+    ctx->test_wait_ns = 0;
     const int grid = (int)(n_items < slots ? n_items : slots);
     bioem_launch_begin(ctx, KID_SCORE_TC);
     if (cudaMemsetAsync(ctx->d_work, 0, sizeof(int), ctx->stream) != cudaSuccess)

@@ -9,7 +9,7 @@
 
 namespace {
 
-constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per barrier wait
+constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per barrier wait (default limit)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -34,14 +34,15 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 }
 
 // Wait until the phase of `bar` with parity `parity` has completed.  Gives up (returns false) when
-// another role has raised the abort flag, or after kWaitNs, raising it and the status bit.
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status) {
+// another role has raised the abort flag, or after limit_ns, raising it and the status bit.
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status,
+                                       unsigned long long limit_ns) {
     if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
     for (;;) {
         if (mbar_try(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (globaltimer() - t0 > kWaitNs) {
+        if (globaltimer() - t0 > limit_ns) {
             *abort_flag = 1;
             atomicOr(status, BIOEM_DEV_TIMEOUT);
             return false;
@@ -50,10 +51,10 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile i
 }
 
 // The same wait without the abort flag (draining copies or MMAs in flight before leaving).
-__device__ __noinline__ bool mbar_drain(uint32_t bar, uint32_t parity) {
+__device__ __noinline__ bool mbar_drain(uint32_t bar, uint32_t parity, unsigned long long limit_ns) {
     const unsigned long long t0 = globaltimer();
     while (!mbar_try(bar, parity))
-        if (globaltimer() - t0 > kWaitNs) return false;
+        if (globaltimer() - t0 > limit_ns) return false;
     return true;
 }
 
