@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libbioem_gb300.so")
 SOURCES = ["abi.cu", "prep_project.cu", "score.cu", "cnn.cu", "gemm.cu", "ensemble.cu", "peak.cu", "score_tc.cu"]
-HEADERS = [os.path.join(CSRC, "bioem_internal.cuh"), os.path.join(CSRC, "tc_util.cuh"),
+HEADERS = [os.path.join(CSRC, "bioem_internal.cuh"), os.path.join(CSRC, "tc_util.cuh"), os.path.join(CSRC, "rdft16.cuh"),
            os.path.join(ROOT, "include", "bioem.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC,-O2",

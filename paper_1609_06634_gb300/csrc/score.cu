@@ -25,6 +25,7 @@
 #include <mutex>
 
 #include "bioem_internal.cuh"
+#include "rdft16.cuh"
 
 namespace {
 
@@ -171,7 +172,14 @@ struct Cfg {
     static constexpr int NCOL = PACK ? NC : H;      // stage-A column tasks per pair
     static constexpr int TASKS_A = PB * NCOL;       // stage-A column tasks per batch
     static constexpr size_t SM_Z = PACK ? SM_Z_PACKED : 0;
-    static constexpr size_t SMEM = SM_BASE + SM_Z;
+    // The dy = +SMAX row by real transforms (the 128 px, +-16 px instance): jobs (pair, Re / Im,
+    // kx sub-sequence) on the last PB 2 R threads, each a real 16-point transform recombined into the
+    // SMAX + 1 even (cosine) or odd (sine) outputs, summed over sub-sequences by lane shuffles; a
+    // direct sum costs ~60 multiply-adds per output instead.
+    static constexpr bool DIRFFT = PACK && N == 128 && SMAX == 16 && THREADS == 512 && PB == 8;
+    static constexpr size_t SM_DTW = DIRFFT ? (size_t)2 * R * (SMAX + 1) * sizeof(float2) : 0;
+    static constexpr size_t SM_DSUM = DIRFFT ? (size_t)PB * 2 * (SMAX + 1) * sizeof(float) : 0;
+    static constexpr size_t SMEM = SM_BASE + SM_Z + SM_DTW + SM_DSUM;
     static_assert(SMEM <= kScoreSmemLimit, "dynamic shared memory per block");
 };
 
@@ -281,6 +289,7 @@ __device__ __forceinline__ float loglik_t(float rho, int* status) {
 template <class C>
 __device__ __forceinline__ void score_tail(const float2* __restrict__ q_s, const float2* __restrict__ twc_s,
                                            float* row_t, float* row_s, int* row_d, float* dir_t,
+                                           const float2* __restrict__ dtw, float* dsum,
                                            const float2* __restrict__ gtw, int p0, int hi, int s, float c1,
                                            float* __restrict__ rec_t, float* __restrict__ rec_s,
                                            int* __restrict__ rec_d, int* __restrict__ status) {
@@ -335,10 +344,56 @@ __device__ __forceinline__ void score_tail(const float2* __restrict__ q_s, const
         row_s[tid] = ssum;
         row_d[tid] = arg;
     }
+    // ---------------- the dy = +SMAX row by real transforms (see Cfg::DIRFFT)
+    if constexpr (C::DIRFFT) {
+        constexpr int NJ = C::PB * 2 * C::R;   // jobs: (pair j, component c, sub-sequence b)
+        static_assert(C::R == 8 && NJ % 32 == 0 && NJ <= C::THREADS, "one job per thread, whole warps");
+        const int tj = tid - (C::THREADS - NJ);
+        const int b = tj & 7, c = (tj >> 3) & 1, j = tj >> 4;
+        const float2* qrow = q_s + ((size_t)j * NS + 2 * SMAX) * C::QS;
+        if (tj >= 0) {
+            float x[8], yr[9], yi[9], a17[SMAX + 1];
+#pragma unroll
+            for (int a = 0; a < 8; ++a) {
+                const float2 v = qrow[b + 8 * a];
+                x[a] = c ? v.y : v.x;
+            }
+            // packed column 0 = (Q(dy, 0), Q(dy, N/2)): weight 1 (the table carries 2), the Nyquist
+            // part enters as (-1)^dx Q(dy, N/2) below
+            if (b == 0) x[0] = c ? 0.f : 0.5f * x[0];
+            rdft16(x, yr, yi);
+#pragma unroll
+            for (int k = 0; k <= SMAX; ++k) a17[k] = 0.f;
+            recombine<SMAX + 1>(a17, yr, yi, dtw + (c * C::R + b) * (SMAX + 1));
+#pragma unroll
+            for (int k = 0; k <= SMAX; ++k) {
+                a17[k] += __shfl_xor_sync(0xffffffffu, a17[k], 1);
+                a17[k] += __shfl_xor_sync(0xffffffffu, a17[k], 2);
+                a17[k] += __shfl_xor_sync(0xffffffffu, a17[k], 4);
+            }
+            if (b == 0) {
+#pragma unroll
+                for (int k = 0; k <= SMAX; ++k) dsum[(j * 2 + c) * (SMAX + 1) + k] = a17[k];
+            }
+            __syncwarp();
+            // lane (c, b) of pair j: dx = b and b + 8 (and 16 for b = 0), sign + for c = 0, - for c = 1
+            const float qn = qrow[0].y;
+            const bool row_ok = SMAX <= s;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const int dx = r == 0 ? b : (r == 1 ? b + 8 : 2 * 8);
+                if ((r == 2 && b != 0) || (c == 1 && dx == 0)) continue;
+                const float cv = dsum[(j * 2) * (SMAX + 1) + dx], sv = dsum[(j * 2 + 1) * (SMAX + 1) + dx];
+                const float rho = cv + (c ? sv : -sv) + ((dx & 1) ? -qn : qn);
+                const int dxs = c ? -dx : dx;
+                dir_t[j * NS + dxs + SMAX] = (row_ok && abs(dxs) <= s) ? loglik_t(rho, status) : INFINITY;
+            }
+        }
+    }
     // ---------------- the dy = +SMAX row, one output per task, evaluated directly; the
     // threads without a stage-B row (tid >= PB NROW) take the first outputs so that few
     // threads with a row get two
-    if (active) {
+    if (active && !C::DIRFFT) {
 #pragma unroll 1
         for (int i = (tid + C::THREADS - C::PB * NROW * C::BSPLIT) % C::THREADS; i < C::NDIR; i += C::THREADS) {
             const int j = i / NS;
@@ -409,6 +464,8 @@ __device__ __forceinline__ void score_item(unsigned char* smem, const float2* __
     float* row_s = row_t + C::PB * NROW * C::BSPLIT;
     int* row_d = reinterpret_cast<int*>(row_s + C::PB * NROW * C::BSPLIT);
     float* dir_t = reinterpret_cast<float*>(row_d + C::PB * NROW * C::BSPLIT);
+    float2* dtw = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(smem) + C::SM_BASE + C::SM_Z);
+    float* dsum = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(dtw) + C::SM_DTW);
 
     const int tid = threadIdx.x;
     const bool active = tid < C::THREADS;
@@ -422,6 +479,19 @@ __device__ __forceinline__ void score_item(unsigned char* smem, const float2* __
         const float4* src = reinterpret_cast<const float4*>(img);
         float4* dst = reinterpret_cast<float4*>(img_s);
         for (int i = tid; i < N * H / 2; i += blockDim.x) dst[i] = __ldg(src + i);
+        if constexpr (C::DIRFFT) {
+            // (T1, T2) x 2 (the weight of kx != 0) for component c, sub-sequence b, output dx
+            const float2* cwN = cw_table<N>();
+            for (int i = tid; i < 2 * C::R * (SMAX + 1); i += blockDim.x) {
+                const int c = i / (C::R * (SMAX + 1)), b = (i / (SMAX + 1)) % C::R, dx = i % (SMAX + 1);
+                const int u = dx & 15;
+                const bool cj = u > 8;
+                const float2 w = cwN[(b * dx) % N];   // (cos, sin) of 2 pi b dx / N
+                const float t1 = c == 0 ? w.x : w.y;
+                const float t2 = c == 0 ? (cj ? w.y : -w.y) : (cj ? -w.x : w.x);
+                dtw[i] = make_float2(2.f * t1, 2.f * t2);
+            }
+        }
     }
     __syncthreads();
     for (int p0 = lo; p0 < hi; p0 += C::PB) {
@@ -458,7 +528,8 @@ __device__ __forceinline__ void score_item(unsigned char* smem, const float2* __
             }
         }
         __syncthreads();
-        score_tail<C>(q_s, twc_s, row_t, row_s, row_d, dir_t, gtw, p0, hi, s, c1, rec_t, rec_s, rec_d, status);
+        score_tail<C>(q_s, twc_s, row_t, row_s, row_d, dir_t, dtw, dsum, gtw, p0, hi, s, c1, rec_t, rec_s, rec_d,
+                      status);
     }
 }
 
