@@ -255,7 +255,10 @@ __global__ void __launch_bounds__(kThreads) k_project(const float4* __restrict__
     __shared__ float bx_t[CH][NB], by_t[CH][NB];
     __shared__ __align__(16) float gx[CH][N];
     __shared__ __align__(16) float gy[CH][N];
-    __shared__ double ax[CH], ay[CH];
+    // per atom and axis, u_j = (edge_j - a) / (sigma sqrt 2) = j D - A as float pairs (hi + lo), so the
+    // table below runs in FP32 (an FMA forms j D_hi - A_hi exactly before rounding) with the accuracy
+    // of a float64 evaluation of u rounded to float
+    __shared__ float axh[CH], axl[CH], ayh[CH], ayl[CH];
     __shared__ float aw[CH];
 
     const int q = blockIdx.x;
@@ -275,26 +278,33 @@ __global__ void __launch_bounds__(kThreads) k_project(const float4* __restrict__
 #pragma unroll
         for (int j = 0; j < TL; ++j) acc[i][j] = 0.f;
     const double inv = 1.0 / (sigma * 1.4142135623730951);
+    const double dd = pixel * inv;                 // D: the pixel in units of sigma sqrt 2
+    const float d_hi = (float)dd, d_lo = (float)(dd - (double)d_hi);
+    const double a_off = (0.5 * N + 0.5) * pixel;  // edge_j = j pixel - a_off
 
     for (int a0 = 0; a0 < n_atoms; a0 += CH) {
         const int na = min(CH, n_atoms - a0);
         for (int a = threadIdx.x; a < CH; a += blockDim.x) {
             if (a < na) {
                 const float4 p = atoms[a0 + a];
-                ax[a] = rot[0] * p.x + rot[1] * p.y + rot[2] * p.z;
-                ay[a] = rot[3] * p.x + rot[4] * p.y + rot[5] * p.z;
+                const double ax = ((rot[0] * p.x + rot[1] * p.y + rot[2] * p.z) + a_off) * inv;
+                const double ay = ((rot[3] * p.x + rot[4] * p.y + rot[5] * p.z) + a_off) * inv;
+                axh[a] = (float)ax;
+                axl[a] = (float)(ax - (double)axh[a]);
+                ayh[a] = (float)ay;
+                ayl[a] = (float)(ay - (double)ayh[a]);
                 aw[a] = p.w;
             } else {
-                ax[a] = 1.0e30; ay[a] = 1.0e30; aw[a] = 0.f;
+                axh[a] = 1.0e30f; axl[a] = 0.f; ayh[a] = 1.0e30f; ayl[a] = 0.f; aw[a] = 0.f;
             }
         }
         __syncthreads();
         // boundary table: erfc(|u|) with the sign of u stored in the sign of the entry
         for (int i = threadIdx.x; i < CH * NB; i += blockDim.x) {
             const int a = i / NB, j = i - (i / NB) * NB;
-            const double edge = ((double)(j - N / 2) - 0.5) * pixel;
-            const float ux = (float)((edge - ax[a]) * inv);
-            const float uy = (float)((edge - ay[a]) * inv);
+            const float fj = (float)j;
+            const float ux = fmaf(fj, d_hi, -axh[a]) + fmaf(fj, d_lo, -axl[a]);
+            const float uy = fmaf(fj, d_hi, -ayh[a]) + fmaf(fj, d_lo, -ayl[a]);
             const float ex = erfcf(fabsf(ux)), ey = erfcf(fabsf(uy));
             // the sign bit carries the sign of u, also when erfc underflows to zero
             bx_t[a][j] = __int_as_float(__float_as_int(ex) | (ux < 0.f ? (int)0x80000000 : 0));
