@@ -669,16 +669,21 @@ def bench_proposal(args):
     # joint bin is the exact coarse scan without the network
     n_joint = cfg.n_coarse * cfg.n_defocus
     two_stage = {}
-    for k1, keep in ((1024, cfg.top_k), (4096, cfg.top_k), (4096, 2 * cfg.top_k), (n_joint, cfg.top_k)):
+    # (network top K1, re-rank grid level, bins kept for the fine grid)
+    variants = ((4096, cfg.coarse_level, cfg.top_k), (n_joint, cfg.coarse_level, cfg.top_k),
+                (1024, cfg.coarse_level + 1, cfg.top_k), (4096, cfg.coarse_level + 1, cfg.top_k),
+                (4096, cfg.coarse_level + 1, 2 * cfg.top_k))
+    for k1, level, keep in variants:
         t0 = time.perf_counter()
         if k1 < n_joint:
             big = net.propose(x, k1)[0].cpu().numpy().astype(np.int64)
         else:
             big = proposal.all_bins(cfg.n_infer, cfg)
-        rr = proposal.rerank_coarse(ctx, im, atoms[0], big, cfg, keep)
+        rr = proposal.rerank_coarse(ctx, im, atoms[0], big, cfg, keep, level=level)
         t_rr = time.perf_counter() - t0
         res_rr = proposal.score_cells(ctx, im, atoms[0], rr["bins"], cfg)
-        two_stage[(k1, keep)] = (rr, t_rr, res_rr, float(np.mean([t in b for t, b in zip(truth, rr["bins"])])))
+        two_stage[(k1, level, keep)] = (rr, t_rr, res_rr,
+                                        float(np.mean([t in b for t, b in zip(truth, rr["bins"])])))
     # judge: the full fine grid (294,912 orientations x 8 PSFs) for every inference image, scanned in
     # chunks of orientations (project, score, fold into per-image accumulators); random proposals
     torch.cuda.synchronize()
@@ -700,10 +705,11 @@ def bench_proposal(args):
     per_img_prop = (t_prop + res["seconds"]) / cfg.n_infer
     per_img_full = t_full / cfg.n_infer
     reranked = []
-    for (k1, keep), (rr, t_rr, res_rr, recall_rr) in two_stage.items():
+    for (k1, level, keep), (rr, t_rr, res_rr, recall_rr) in two_stage.items():
         kept_rr = res_rr["logP"] - full_logP
-        per_img_rr = (t_rr + res_rr["seconds"]) / cfg.n_infer
-        reranked.append({"network_top": k1 if k1 < n_joint else "all (no network)", "fine_bins": keep,
+        per_img_rr = (t_prop + t_rr + res_rr["seconds"]) / cfg.n_infer
+        reranked.append({"network_top": k1 if k1 < n_joint else "all (no network)", "rerank_level": level,
+                         "rerank_orientations_per_bin": 8 ** (level - cfg.coarse_level), "fine_bins": keep,
                          "recall_of_true_bin": recall_rr,
                          "coarse_evals_per_image": rr["evals"] / cfg.n_infer,
                          "fine_evals_per_image": res_rr["evals"] / cfg.n_infer, "rerank_s": t_rr,

@@ -99,6 +99,23 @@ def train_redrawn(ctx: Context, net: CNN, atoms_dev: list, d: dict, cfg, epochs:
     return losses
 
 
+def _cell_lists(bins: np.ndarray, pos: np.ndarray, n_defocus: int, n_b: int, kids: int):
+    """Per-image parameter-set lists (CSR) of the joint bins whose cells are in the current wave:
+    bin (cell, defocus d) -> sets ((pos[cell] * kids + j) * n_ctf + d * n_b + b) for its kids child
+    orientations j and every B index b, in image-major, bin-major order.  Returns (mask [n, K] of
+    the bins in this wave, offsets [n + 1], flat set indices)."""
+    cells, dd = bins // n_defocus, bins % n_defocus
+    pc = pos[cells]
+    mask = pc >= 0
+    nctf = n_defocus * n_b
+    sel_p, sel_d = pc[mask], dd[mask]                                               # row-major: by image
+    base = (sel_p * kids)[:, None] + np.arange(kids)[None, :]                       # [n_sel, kids]
+    flat = ((base * nctf + (sel_d * n_b)[:, None])[:, :, None] + np.arange(n_b)).reshape(-1)
+    counts = mask.sum(axis=1) * kids * n_b
+    off = np.concatenate([[0], np.cumsum(counts)])
+    return mask, off, flat
+
+
 def score_cells(ctx: Context, images, atoms_dev, bins: np.ndarray, cfg, wave: int = 256) -> dict:
     """ln P of every image over the union of its joint cells bins[i] (coarse cell * n_defocus + defocus
     bin), each cell expanded to its fine orientations x the cell's defocus x every B.  ln P is
@@ -114,8 +131,8 @@ def score_cells(ctx: Context, images, atoms_dev, bins: np.ndarray, cfg, wave: in
     kids = cfg.children
     S = (2 * cfg.max_shift + 1) ** 2
     log_norm = math.log(len(fine_q) * nctf * S)
-    cells = bins // nd
-    used = np.unique(cells)
+    bins = np.asarray(bins, dtype=np.int64)
+    used = np.unique(bins // nd)
     acc = torch.empty((n_img, 2), dtype=torch.float64, device=dev)
     first = True
     evals = 0
@@ -128,24 +145,11 @@ def score_cells(ctx: Context, images, atoms_dev, bins: np.ndarray, cfg, wave: in
         child = workloads.hopf_children(cfg.coarse_level, cfg.fine_level, wc).ravel()
         q = torch.from_numpy(np.ascontiguousarray(fine_q[child])).to(dev)
         ps = project_model(ctx, atoms_dev, cfg.sigma_A, q, rows, cfg.npix, cfg.pixel_A)
-        # per image: the (cell, defocus) bins of this wave -> fine sets (pos * kids + j) * nctf + d * nb + b
-        lists = []
-        for i in range(n_img):
-            sel = bins[i][pos[cells[i]] >= 0]
-            if len(sel) == 0:
-                lists.append(np.zeros(0, dtype=np.int64))
-                continue
-            p = pos[sel // nd]
-            dd = sel % nd
-            j = np.arange(kids)
-            idx = ((p[:, None, None] * kids + j[None, :, None]) * nctf + dd[:, None, None] * nb
-                   + np.arange(nb)[None, None, :])
-            lists.append(idx.ravel())
-        counts = np.array([len(x) for x in lists])
+        _, off, flat = _cell_lists(bins, pos, nd, nb, kids)
+        counts = np.diff(off)
         evals += int(counts.sum())
-        off = torch.from_numpy(np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)).to(dev)
-        flat = torch.from_numpy(np.concatenate(lists).astype(np.int32)).to(dev)
-        score_gathered(ctx, images, ps, cfg.max_shift, off, flat, max(1, int(counts.max())), acc, first)
+        score_gathered(ctx, images, ps, cfg.max_shift, torch.from_numpy(off.astype(np.int32)).to(dev),
+                       torch.from_numpy(flat.astype(np.int32)).to(dev), max(1, int(counts.max())), acc, first)
         first = False
         ps.close()
     logp = acc_logP(ctx, acc, log_norm)
@@ -154,39 +158,39 @@ def score_cells(ctx: Context, images, atoms_dev, bins: np.ndarray, cfg, wave: in
             "cells": int(len(used))}
 
 
-def rerank_coarse(ctx: Context, images, atoms_dev, bins: np.ndarray, cfg, keep: int, wave: int = 2304) -> dict:
-    """Exact re-ranking of proposed joint bins: bin (coarse cell, defocus) is scored at the cell's own
-    coarse grid orientation x its defocus x every B (ln sum over B and displacements of L, the
-    closed-form likelihood of the scoring path); per image the `keep` best bins are returned, best
-    first.  The cells are projected in waves of `wave`."""
+def rerank_coarse(ctx: Context, images, atoms_dev, bins: np.ndarray, cfg, keep: int, wave: int = 2304,
+                  level: int | None = None) -> dict:
+    """Exact re-ranking of proposed joint bins: bin (coarse cell, defocus) is scored at the cell's
+    orientations of Hopf level `level` (default: the coarse level itself, one orientation per cell;
+    one level finer: the cell's 8 children) x its defocus x every B, as ln sum over them and over the
+    displacements of L (the closed-form likelihood of the scoring path, summed by the library); per
+    image the `keep` best bins are returned, best first.  The cells are projected in waves."""
     import workloads
     torch = _torch()
     dev = ctx.device
     nd, nb = cfg.n_defocus, len(cfg.bfactors)
-    nctf = nd * nb
-    coarse_q = workloads.hopf_grid(cfg.coarse_level).astype(np.float32)
+    level = cfg.coarse_level if level is None else level
+    kids = 8 ** (level - cfg.coarse_level)
+    grid_q = workloads.hopf_grid(level).astype(np.float32)
     bins = np.asarray(bins, dtype=np.int64)
-    cells, dd = bins // nd, bins % nd
     scores = np.full(bins.shape, -np.inf)
-    used = np.unique(cells)
+    used = np.unique(bins // nd)
+    wave = max(1, wave // kids)
     evals = 0
     t0 = time.perf_counter()
     for w0 in range(0, len(used), wave):
         wc = used[w0:w0 + wave]
         pos = np.full(cfg.n_coarse, -1, dtype=np.int64)
         pos[wc] = np.arange(len(wc))
-        ps = project_model(ctx, atoms_dev, cfg.sigma_A, torch.from_numpy(np.ascontiguousarray(coarse_q[wc])).to(dev),
+        child = workloads.hopf_children(cfg.coarse_level, level, wc).ravel() if kids > 1 else wc
+        ps = project_model(ctx, atoms_dev, cfg.sigma_A, torch.from_numpy(np.ascontiguousarray(grid_q[child])).to(dev),
                            cfg.ctf_rows(), cfg.npix, cfg.pixel_A)
-        pc = pos[cells]
-        mask = pc >= 0                                   # [n_img, K]: bins of this wave
-        base = (pc * nctf + dd * nb)[mask]               # row-major: grouped by image
-        flat = (base[:, None] + np.arange(nb)[None, :]).ravel()
-        counts = mask.sum(axis=1) * nb
-        off = torch.from_numpy(np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)).to(dev)
-        v = score_gathered_pairs(ctx, images, ps, cfg.max_shift, off,
+        mask, off, flat = _cell_lists(bins, pos, nd, nb, kids)
+        counts = np.diff(off)
+        v = score_gathered_pairs(ctx, images, ps, cfg.max_shift, torch.from_numpy(off.astype(np.int32)).to(dev),
                                  torch.from_numpy(flat.astype(np.int32)).to(dev), max(1, int(counts.max())))
-        # ln sum over the B-factors of each bin (the library's log-sum-exp; the host only orders bins)
-        scores[mask] = group_logsumexp(ctx, v, nb).cpu().numpy()
+        # ln sum over each bin's children and B-factors (the library's log-sum-exp; the host orders bins)
+        scores[mask] = group_logsumexp(ctx, v, kids * nb).cpu().numpy()
         evals += int(counts.sum())
         ps.close()
     order = np.argsort(-scores, axis=1, kind="stable")[:, :keep]

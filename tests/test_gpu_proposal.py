@@ -86,6 +86,25 @@ def test_proposal_end_to_end(env):
     print(f"re-ranked: recall {recall_rr:.3f} (network top-k {recall:.3f}); kept mean {np.mean(kept_rr):.3f}")
     assert recall_rr >= recall - 1.0 / cfg.n_infer
     assert np.mean(kept_rr) >= np.mean(kept_prop) - 1e-6
+    # the same re-ranking over each cell's 8 children one level finer: its score of a bin is the
+    # log-sum-exp, over those orientations and both B, of the library's per-pair values
+    rr3 = proposal.rerank_coarse(ctx, im, atoms[0], big, cfg, cfg.top_k, level=cfg.coarse_level + 1)
+    assert rr3["evals"] == cfg.n_infer * 4 * cfg.top_k * 8 * len(cfg.bfactors)
+    assert all(set(r) <= set(b) for r, b in zip(rr3["bins"], big))
+    w = 3
+    cells = big[w] // cfg.n_defocus
+    q3 = workloads.hopf_grid(cfg.coarse_level + 1).astype(np.float32)
+    kids = workloads.hopf_children(cfg.coarse_level, cfg.coarse_level + 1, cells)        # [K, 8]
+    ps3 = bioem.project_model(ctx, atoms[0], cfg.sigma_A, torch.from_numpy(q3[kids.ravel()]).to(dev),
+                              cfg.ctf_rows(), cfg.npix, cfg.pixel_A)
+    im1 = bioem.prepare_images(ctx, x[w:w + 1].contiguous(), cfg.pixel_A)
+    _, plse = bioem.score_pairs(ctx, im1, ps3, cfg.max_shift)
+    plse = plse.cpu().numpy()[0].reshape(len(cells), 8, cfg.n_defocus, len(cfg.bfactors))
+    dd = big[w] % cfg.n_defocus
+    v = plse[np.arange(len(cells)), :, dd, :].reshape(len(cells), -1)
+    score = v.max(axis=1) + np.log(np.exp(v - v.max(axis=1, keepdims=True)).sum(axis=1))
+    want = big[w][np.argsort(-score, kind="stable")[:cfg.top_k]]
+    np.testing.assert_array_equal(np.sort(rr3["bins"][w]), np.sort(want))
 
 
 def test_gathered_pairs_match_score_pairs(env):
