@@ -84,8 +84,8 @@ def test_proposal_end_to_end(env):
     kept_rr = prop_rr["logP"] - full["logP"]
     recall_rr = np.mean([t in b for t, b in zip(truth, rr["bins"])])
     print(f"re-ranked: recall {recall_rr:.3f} (network top-k {recall:.3f}); kept mean {np.mean(kept_rr):.3f}")
-    assert recall_rr >= recall - 1.0 / cfg.n_infer
-    assert np.mean(kept_rr) >= np.mean(kept_prop) - 1e-6
+    # the coarse grid point is only a proxy for a cell's fine mass: better than random cells
+    assert np.mean(kept_rr) > np.mean(kept_rand) + 1.0, (np.mean(kept_rr), np.mean(kept_rand))
     # the same re-ranking over each cell's 8 children one level finer: its score of a bin is the
     # log-sum-exp, over those orientations and both B, of the library's per-pair values
     rr3 = proposal.rerank_coarse(ctx, im, atoms[0], big, cfg, cfg.top_k, level=cfg.coarse_level + 1)
@@ -107,6 +107,11 @@ def test_proposal_end_to_end(env):
     kth = np.sort(score)[::-1][cfg.top_k - 1]
     by_bin = dict(zip(big[w].tolist(), score.tolist()))
     assert all(by_bin[b] >= kth - 1e-3 for b in rr3["bins"][w].tolist())
+    # here that level is the fine grid itself, so a bin's score is its fine posterior mass and the k
+    # best bins keep the most mass any k of the wide proposal can: at least the network's top k
+    assert cfg.coarse_level + 1 == cfg.fine_level
+    kept_rr3 = proposal.score_cells(ctx, im, atoms[0], rr3["bins"], cfg)["logP"] - full["logP"]
+    assert np.all(kept_rr3 >= kept_prop - 1e-6) and np.all(kept_rr3 >= kept_rr - 1e-6)
 
 
 def test_gathered_pairs_match_score_pairs(env):
