@@ -71,7 +71,7 @@ def kernel_source_sha(kernel: str) -> str:
 #   k_score: per evaluated pair, from one launch of 2048 images x 4608 sets (above L2), scaled by
 #            pairs to the bench's launches (profiles/k_score_throughput.md).
 #   k_score_gemm: per launch of the precision workloads (64 images x 6912 sets, +-4 px).
-K_SCORE_TRAFFIC = {"source_sha256": "f7c59412dc327757fa81aa0019b32c26097be974ce46c6738e7d371a235d31c7", "bytes_per_pair": (1558311424 + 117285632) / (2048 * 4608)}
+K_SCORE_TRAFFIC = {"source_sha256": "2cc4811913348c6e2104fe476a4e3784951ce4acbe88f8cba24d3266a0c95a2f", "bytes_per_pair": (1555190784 + 116923648) / (2048 * 4608)}
 K_SCORE_GEMM_TRAFFIC = {"source_sha256": "", "bytes_per_launch": {
     '128/bf16x2': 3794691556, '128/fp16x2': 5033599431, '128/bf16x2_real': 4005294820, '128/fp16x2_real': 5370143033,
     '64/bf16x2': 895775374, '64/fp16x2': 896910507, '64/bf16x2_real': 868407154, '64/fp16x2_real': 869934222}}
