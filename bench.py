@@ -672,7 +672,7 @@ def bench_proposal(args):
     # (network top K1, re-rank grid level, bins kept for the fine grid)
     variants = ((4096, cfg.coarse_level, cfg.top_k), (n_joint, cfg.coarse_level, cfg.top_k),
                 (1024, cfg.coarse_level + 1, cfg.top_k), (4096, cfg.coarse_level + 1, cfg.top_k),
-                (4096, cfg.coarse_level + 1, 2 * cfg.top_k))
+                (8192, cfg.coarse_level + 1, cfg.top_k))
     for k1, level, keep in variants:
         t0 = time.perf_counter()
         if k1 < n_joint:
