@@ -72,9 +72,9 @@ def kernel_source_sha(kernel: str) -> str:
 #            pairs to the bench's launches (profiles/k_score_throughput.md).
 #   k_score_gemm: per launch of the precision workloads (64 images x 6912 sets, +-4 px).
 K_SCORE_TRAFFIC = {"source_sha256": "2cc4811913348c6e2104fe476a4e3784951ce4acbe88f8cba24d3266a0c95a2f", "bytes_per_pair": (1555190784 + 116923648) / (2048 * 4608)}
-K_SCORE_GEMM_TRAFFIC = {"source_sha256": "", "bytes_per_launch": {
-    '128/bf16x2': 3794691556, '128/fp16x2': 5033599431, '128/bf16x2_real': 4005294820, '128/fp16x2_real': 5370143033,
-    '64/bf16x2': 895775374, '64/fp16x2': 896910507, '64/bf16x2_real': 868407154, '64/fp16x2_real': 869934222}}
+K_SCORE_GEMM_TRAFFIC = {"source_sha256": "44a4cc65e9cce910a31c5422b70798713a4e53873ab1b4fba53a1ce75cd3d37c", "bytes_per_launch": {
+    '128/bf16x2': 3527298048, '128/fp16x2': 3544666112, '128/bf16x2_real': 3473174528, '128/fp16x2_real': 3496760576,
+    '64/bf16x2': 895239040, '64/fp16x2': 895184640, '64/bf16x2_real': 868600448, '64/fp16x2_real': 868093952}}
 K_SCORE_TC_TRAFFIC = {"source_sha256": "", "bytes_per_pair": None}
 
 
