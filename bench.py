@@ -13,6 +13,12 @@ model through the library's synthetic-map entry point plus seeded shifts, normal
 and noise.  Under torchrun every rank scores its own 2048 images against the full grid (weak
 scaling, no data-path collective).
 
+The scoring form is the FP32 one (pruned FFT on the CUDA cores); `--precision fp16x2_fft` times the
+same path with its column transforms on the tensor cores.  Other workloads: `--workload precision`
+(split-precision tensor-core forms at +-4 px), `shifts` (the shift-window sweep), `batched`
+(models x mixed-size stacks in one graph launch) and `proposal` (the learned proposal, judged on
+every image against the full fine grid).
+
 `--impl reference` times the FP64 CPU oracle instead, on a bounded sample of the same workload.
 """
 from __future__ import annotations
