@@ -220,13 +220,23 @@ __device__ __forceinline__ void stage_a_column(float2 (&acc)[C::NS], const float
         img_col += H;
         ps_col += H;
         fft_dif<L>(x);
+        // twc[b][SMAX -+ d] = W^(-+b d) are complex conjugates: one load serves dy = +d and -d
         const float2* tw = twc + b * NS;
 #pragma unroll
-        for (int mi = 0; mi < NS; ++mi) {
-            const int u = bitrev(pmod(mi - SMAX, L), ilog2(L));
-            const float2 w = tw[mi];
-            acc[mi].x = fmaf(w.x, x[u].x, fmaf(-w.y, x[u].y, acc[mi].x));
-            acc[mi].y = fmaf(w.x, x[u].y, fmaf(w.y, x[u].x, acc[mi].y));
+        for (int d = 0; d <= SMAX; ++d) {
+            const float2 w = tw[SMAX + d];
+            {
+                const int mi = SMAX + d;
+                const int u = bitrev(pmod(mi - SMAX, L), ilog2(L));
+                acc[mi].x = fmaf(w.x, x[u].x, fmaf(-w.y, x[u].y, acc[mi].x));
+                acc[mi].y = fmaf(w.x, x[u].y, fmaf(w.y, x[u].x, acc[mi].y));
+            }
+            if (d > 0) {
+                const int mi = SMAX - d;
+                const int u = bitrev(pmod(mi - SMAX, L), ilog2(L));
+                acc[mi].x = fmaf(w.x, x[u].x, fmaf(w.y, x[u].y, acc[mi].x));
+                acc[mi].y = fmaf(w.x, x[u].y, fmaf(-w.y, x[u].x, acc[mi].y));
+            }
         }
     }
 }
@@ -244,12 +254,20 @@ __device__ __forceinline__ void stage_b_row(float (&acc)[C::NS], const float2* _
         for (int a = 0; a < L / 2; ++a) x[a] = c_scale(qrow[b + R * a], 2.f);
         if (b == 0) x[0] = make_float2(qrow[0].x, 0.f);   // kx = 0: weight 1, real
         fft_dif_half_zero<L>(x);
-        const float2* tw = twc + b * NS;
+        const float2* tw = twc + b * NS;   // conjugate pairs, as in stage A
 #pragma unroll
-        for (int mi = 0; mi < NS; ++mi) {
-            const int u = bitrev(pmod(mi - SMAX, L), ilog2(L));
-            const float2 w = tw[mi];
-            acc[mi] = fmaf(w.x, x[u].x, fmaf(-w.y, x[u].y, acc[mi]));
+        for (int d = 0; d <= SMAX; ++d) {
+            const float2 w = tw[SMAX + d];
+            {
+                const int mi = SMAX + d;
+                const int u = bitrev(pmod(mi - SMAX, L), ilog2(L));
+                acc[mi] = fmaf(w.x, x[u].x, fmaf(-w.y, x[u].y, acc[mi]));
+            }
+            if (d > 0) {
+                const int mi = SMAX - d;
+                const int u = bitrev(pmod(mi - SMAX, L), ilog2(L));
+                acc[mi] = fmaf(w.x, x[u].x, fmaf(w.y, x[u].y, acc[mi]));
+            }
         }
     }
 }
