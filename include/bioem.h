@@ -350,6 +350,13 @@ void bioem_cnn_free(bioem_cnn* cnn);
  * Errors: INVALID_ARG, CUDA. */
 int bioem_fma_peak(bioem_ctx* ctx, int kind, int reps, double* flops_per_s);
 
+/* t = ln(1 - x) as every scoring kernel evaluates it for x = rho^2, the per-displacement factor of
+ * the closed-form likelihood (Eq. 8 integrated over N, mu and lambda: ln L = kA + kB + (3 - n)/2 t):
+ * a five-term Taylor series for x <= 1/32, the library's log1pf above.  A test hook: d_x [n] and
+ * d_t [n] float32 device arrays, 0 <= x < 1 (x = 1 gives -inf and x > 1 NaN, as log1pf does;
+ * negative x are outside the contract), on the context's stream.  Errors: INVALID_ARG, CUDA. */
+int bioem_ln1m(bioem_ctx* ctx, const float* d_x, long long n, float* d_t);
+
 /* Measurement hooks.  bioem_launch_count: kernels the library has launched with this context
  * since creation or the last reset.  With timing enabled, CUDA events are recorded on the
  * context's stream around every launch; bioem_kernel_time synchronises the stream and returns the

@@ -16,7 +16,7 @@ from ._native import CTF
 
 __all__ = ["BioEMError", "Context", "Images", "ProjSet", "prepare_images", "project_model", "score", "score_all",
            "best_params", "score_pairs", "score_noalloc", "Batch", "autotune", "autotune_load", "CNN", "score_gathered", "acc_logP",
-           "acc_merge", "group_logsumexp", "fma_peak", "synthetic_maps", "ctf_array", "lib"]
+           "acc_merge", "group_logsumexp", "ln1m", "fma_peak", "synthetic_maps", "ctf_array", "lib"]
 
 OK = 0
 ERR_INVALID_ARG, ERR_UNSUPPORTED_SIZE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NUMERIC = -1, -2, -3, -4, -5, -6
@@ -474,6 +474,15 @@ def group_logsumexp(ctx: Context, values, group_len: int):
     n_groups = v.numel() // group_len
     out = torch.empty(n_groups, dtype=torch.float64, device=ctx.device)
     _check(ctx, lib().bioem_group_logsumexp(ctx._h, _ptr(v), n_groups, int(group_len), _ptr(out)), "group_logsumexp")
+    return out
+
+
+def ln1m(ctx: Context, x):
+    """bioem_ln1m: ln(1 - x) for float32 x = rho^2 as the scoring kernels evaluate it (test hook)."""
+    torch = _torch()
+    v = _dev_tensor(x, torch.float32, ctx.device, "x").reshape(-1)
+    out = torch.empty_like(v)
+    _check(ctx, lib().bioem_ln1m(ctx._h, _ptr(v), v.numel(), _ptr(out)), "ln1m")
     return out
 
 

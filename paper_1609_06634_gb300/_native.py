@@ -56,6 +56,7 @@ SIGNATURES = {
     "bioem_acc_logP": (c_int, [c_void_p, c_void_p, c_int, c_double, c_void_p]),
     "bioem_acc_merge": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p]),
     "bioem_group_logsumexp": (c_int, [c_void_p, c_void_p, ctypes.c_longlong, c_int, c_void_p]),
+    "bioem_ln1m": (c_int, [c_void_p, c_void_p, ctypes.c_longlong, c_void_p]),
     "bioem_fma_peak": (c_int, [c_void_p, c_int, c_int, ctypes.POINTER(c_double)]),
     "bioem_score_gathered_pairs": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_int, c_int,
                                            c_void_p]),

@@ -268,16 +268,16 @@ __device__ __forceinline__ Part part_merge(Part a, Part b, float c1) {
     return Part{b.t, b.s + a.s * __expf(c1 * (a.t - b.t)), b.d};
 }
 
-// One displacement's value into a running (t_min, sum, argmin): rho = v inv, t = log1p(-rho^2).
-// Branch-free (the lanes of a warp hold different parameter sets, so a data-dependent branch would
-// serialise both sides on every column), one exponential: e = exp(c1 |t - t_min|) either rescales
+// One displacement's value into a running (t_min, sum, argmin): rho = v inv, t = ln(1 - rho^2).
+// No data-dependent branch apart from ln1m's rarely taken one for rho^2 > 1/32 (the lanes of a warp
+// hold different parameter sets, so a branch would serialise both sides on every column), one exponential: e = exp(c1 |t - t_min|) either rescales
 // the sum to a new minimum (s e + 1) or is the new term (s + e).  r2max collects rho^2 for one
 // |rho| >= 1 check per tile.
 __device__ __forceinline__ void part_add(Part& st, float& r2max, float v, float inv, int j, float c1) {
     const float rho = v * inv;
     const float r2 = rho * rho;
     r2max = fmaxf(r2max, r2);
-    const float tv = log1pf(-fminf(r2, 1.0f - 5.9604645e-8f));
+    const float tv = ln1m(fminf(r2, 1.0f - 5.9604645e-8f));
     const bool lower = tv < st.t;
     const float e = __expf(c1 * fabsf(tv - st.t));   // the first value: exp(-inf) = 0, s = 0 * 0 + 1
     st.s = lower ? fmaf(st.s, e, 1.f) : st.s + e;

@@ -158,10 +158,15 @@ struct Cfg {
     static constexpr int NDIR = PB * NS;       // outputs of the dy = +SMAX row, evaluated directly
     static constexpr size_t SM_IMG = (size_t)N * H * sizeof(float2);
     static constexpr size_t SM_Q = (size_t)PB * NS * QS * sizeof(float2);
-    static constexpr size_t SM_TWC = (size_t)R * NS * sizeof(float2);
+    static constexpr size_t SM_QA = (SM_Q + 15) / 16 * 16;   // the twiddle table starts 16-byte aligned
+    // twiddle table twc[b][d] = W_N^(b d), d = 0..SMAX (the outputs -d use the conjugate), rows of
+    // an even length TWS so that pairs (d, d + 1), d even, are read as one 16-byte load
+    static constexpr int TWS = 2 * ((SMAX + 2) / 2);
+    static constexpr size_t SM_TWC = (size_t)R * TWS * sizeof(float2);
+    static_assert((SM_IMG + SM_QA) % 16 == 0 && (TWS * sizeof(float2)) % 16 == 0, "16-byte twiddle pairs");
     static constexpr size_t SM_ROW = (size_t)PB * NROW * BSPLIT * (2 * sizeof(float) + sizeof(int));
     static constexpr size_t SM_DIR = (size_t)NDIR * sizeof(float);
-    static constexpr size_t SM_BASE = SM_IMG + SM_Q + SM_TWC + SM_ROW + SM_DIR;
+    static constexpr size_t SM_BASE = SM_IMG + SM_QA + SM_TWC + SM_ROW + SM_DIR;
     // Packed edge columns: for real images and projections the product conj(O) C is Hermitian in
     // ky on the kx = 0 and kx = N/2 columns, so both columns' stage-A outputs are real, and one
     // complex transform of Z(ky) = P(ky, 0) + i P(ky, N/2) gives Q(dy, 0) as its real part and
@@ -185,7 +190,8 @@ struct Cfg {
 
 // Stage A for one column kx of one pair: Q(dy, kx) for dy = -SMAX..SMAX, with the rows ky = b + R a
 // of sub-sequence b transformed by an in-register FFT and recombined with the twiddles
-// twc[b][m] = W_N^(b (m - SMAX)) (shared memory, the same address for every thread: broadcast).
+// twc[b][d] = W_N^(b d), d = 0..SMAX, and their conjugates (shared memory, the same address for every
+// thread: broadcast).
 // The projection column is read from global memory one sub-sequence ahead of its use.  With zcol
 // set (the packed edge columns) the inputs are zcol[ky] instead of the product.
 template <class C>
@@ -220,11 +226,11 @@ __device__ __forceinline__ void stage_a_column(float2 (&acc)[C::NS], const float
         img_col += H;
         ps_col += H;
         fft_dif<L>(x);
-        // twc[b][SMAX -+ d] = W^(-+b d) are complex conjugates: one load serves dy = +d and -d
-        const float2* tw = twc + b * NS;
+        // W^(b d) and W^(-b d) are complex conjugates: one twiddle serves dy = +d and -d
+        const float2* tw = twc + b * C::TWS;
 #pragma unroll
         for (int d = 0; d <= SMAX; ++d) {
-            const float2 w = tw[SMAX + d];
+            const float2 w = tw[d];
             {
                 const int mi = SMAX + d;
                 const int u = bitrev(pmod(mi - SMAX, L), ilog2(L));
@@ -254,10 +260,10 @@ __device__ __forceinline__ void stage_b_row(float (&acc)[C::NS], const float2* _
         for (int a = 0; a < L / 2; ++a) x[a] = c_scale(qrow[b + R * a], 2.f);
         if (b == 0) x[0] = make_float2(qrow[0].x, 0.f);   // kx = 0: weight 1, real
         fft_dif_half_zero<L>(x);
-        const float2* tw = twc + b * NS;   // conjugate pairs, as in stage A
+        const float2* tw = twc + b * C::TWS;   // conjugate pairs, as in stage A
 #pragma unroll
         for (int d = 0; d <= SMAX; ++d) {
-            const float2 w = tw[SMAX + d];
+            const float2 w = tw[d];
             {
                 const int mi = SMAX + d;
                 const int u = bitrev(pmod(mi - SMAX, L), ilog2(L));
@@ -299,7 +305,7 @@ __device__ __forceinline__ float loglik_t(float rho, int* status) {
         atomicOr(status, BIOEM_DEV_NUMERIC);
         r2 = 1.0f - 5.9604645e-8f;
     }
-    return log1pf(-r2);
+    return ln1m(r2);
 }
 
 // Stage B (row transforms), the dy = +SMAX row, the likelihood epilogue and the per-pair combine of
@@ -476,8 +482,8 @@ __device__ __forceinline__ void score_item(unsigned char* smem, const float2* __
     constexpr int N = C::N, NC = C::NC, H = C::H, NS = C::NS, SMAX = C::SMAX, NROW = C::NROW;
     float2* img_s = reinterpret_cast<float2*>(smem);
     float2* q_s = reinterpret_cast<float2*>(smem + C::SM_IMG);
-    float2* twc_s = reinterpret_cast<float2*>(smem + C::SM_IMG + C::SM_Q);
-    float2* z_s = twc_s + C::R * NS;   // [PB][N] packed edge columns (C::PACK)
+    float2* twc_s = reinterpret_cast<float2*>(smem + C::SM_IMG + C::SM_QA);
+    float2* z_s = twc_s + C::R * C::TWS;   // [PB][N] packed edge columns (C::PACK)
     float* row_t = reinterpret_cast<float*>(z_s + (C::PACK ? C::PB * N : 0));
     float* row_s = row_t + C::PB * NROW * C::BSPLIT;
     int* row_d = reinterpret_cast<int*>(row_s + C::PB * NROW * C::BSPLIT);
@@ -490,9 +496,9 @@ __device__ __forceinline__ void score_item(unsigned char* smem, const float2* __
     __syncthreads();   // the previous item's readers of shared memory are done
     {
         const float2* cwN = cw_table<N>();
-        for (int i = tid; i < C::R * NS; i += blockDim.x) {
-            const int b = i / NS, m = i - (i / NS) * NS - SMAX;
-            twc_s[i] = cwN[pmod(b * m, N)];
+        for (int i = tid; i < C::R * C::TWS; i += blockDim.x) {
+            const int b = i / C::TWS, d = i - (i / C::TWS) * C::TWS;
+            twc_s[i] = d <= SMAX ? cwN[pmod(b * d, N)] : make_float2(0.f, 0.f);
         }
         const float4* src = reinterpret_cast<const float4*>(img);
         float4* dst = reinterpret_cast<float4*>(img_s);
@@ -1825,6 +1831,22 @@ int bioem_group_logsumexp(bioem_ctx* ctx, const double* d_values, long long n_gr
     k_group_lse<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, ctx->stream>>>(d_values, n_groups, group_len, d_out);
     bioem_launch_end(ctx, KID_LSE_MERGE);
     return bioem_check_cuda(ctx, cudaGetLastError(), "k_group_lse");
+}
+
+__global__ void k_ln1m(const float* __restrict__ x, long long n, float* __restrict__ t) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        t[i] = ln1m(x[i]);
+}
+
+int bioem_ln1m(bioem_ctx* ctx, const float* d_x, long long n, float* d_t) {
+    if (!ctx || n < 0 || (n > 0 && (!d_x || !d_t))) return BIOEM_ERR_INVALID_ARG;
+    if (n == 0) return BIOEM_OK;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return bioem_set_error(ctx, BIOEM_ERR_CUDA, "cudaSetDevice");
+    const long long blocks = (n + 255) / 256;
+    bioem_launch_begin(ctx, KID_LSE_MERGE);
+    k_ln1m<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, ctx->stream>>>(d_x, n, d_t);
+    bioem_launch_end(ctx, KID_LSE_MERGE);
+    return bioem_check_cuda(ctx, cudaGetLastError(), "k_ln1m");
 }
 
 int bioem_acc_logP(bioem_ctx* ctx, const double* d_acc, int n_img, double log_norm, double* d_logP) {

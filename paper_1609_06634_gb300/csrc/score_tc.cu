@@ -122,7 +122,7 @@ __device__ __forceinline__ float tc_loglik(float rho, int* status) {
         atomicOr(status, BIOEM_DEV_NUMERIC);
         r2 = 1.0f - 5.9604645e-8f;
     }
-    return log1pf(-r2);
+    return ln1m(r2);
 }
 
 __device__ __forceinline__ uint32_t pack_half2(float a, float b) {
