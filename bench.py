@@ -55,11 +55,12 @@ CSRC = os.path.join(ROOT, "paper_1609_06634_gb300", "csrc")
 KERNEL_SOURCES = {
     "k_score": (os.path.join(CSRC, "score.cu"), "template <int N_, int SMAX_",
                 "// ---------------------------------------------------------------------------- reductions (float64)",
-                []),
+                [os.path.join(CSRC, "bioem_internal.cuh"), os.path.join(CSRC, "rdft16.cuh")]),
     "k_score_gemm": (os.path.join(CSRC, "gemm.cu"), "struct GemmArgs {", "bool mode_fp16(int mode)",
-                     [os.path.join(CSRC, "tc_util.cuh")]),
+                     [os.path.join(CSRC, "tc_util.cuh"), os.path.join(CSRC, "bioem_internal.cuh")]),
     "k_score_tc": (os.path.join(CSRC, "score_tc.cu"), "namespace tcs {", "int bioem_tc_supported(",
-                   [os.path.join(CSRC, "tc_util.cuh")]),
+                   [os.path.join(CSRC, "tc_util.cuh"), os.path.join(CSRC, "rdft16.cuh"),
+                    os.path.join(CSRC, "bioem_internal.cuh")]),
 }
 
 
@@ -77,10 +78,10 @@ def kernel_source_sha(kernel: str) -> str:
 #   k_score: per evaluated pair, from one launch of 2048 images x 4608 sets (above L2), scaled by
 #            pairs to the bench's launches (profiles/k_score_throughput.md).
 #   k_score_gemm: per launch of the precision workloads (64 images x 6912 sets, +-4 px).
-K_SCORE_TRAFFIC = {"source_sha256": "2cc4811913348c6e2104fe476a4e3784951ce4acbe88f8cba24d3266a0c95a2f", "bytes_per_pair": (1555190784 + 116923648) / (2048 * 4608)}
-K_SCORE_GEMM_TRAFFIC = {"source_sha256": "44a4cc65e9cce910a31c5422b70798713a4e53873ab1b4fba53a1ce75cd3d37c", "bytes_per_launch": {
-    '128/bf16x2': 3527298048, '128/fp16x2': 3544666112, '128/bf16x2_real': 3473174528, '128/fp16x2_real': 3496760576,
-    '64/bf16x2': 895239040, '64/fp16x2': 895184640, '64/bf16x2_real': 868600448, '64/fp16x2_real': 868093952}}
+K_SCORE_TRAFFIC = {"source_sha256": "278a5904c99094af3a3af3804259c98e0b9bec7562a3ebdf818fb72b2a7ec3d8", "bytes_per_pair": (1553092608 + 118595584) / (2048 * 4608)}
+K_SCORE_GEMM_TRAFFIC = {"source_sha256": "8a4ab46e82245e057c6ddb95ab59aade4800f46890ef4318f1b20e5295a9bff0", "bytes_per_launch": {
+    '128/bf16x2': 3568891648, '128/fp16x2': 5365016832, '128/bf16x2_real': 4240276480, '128/fp16x2_real': 5136271360,
+    '64/bf16x2': 895626240, '64/fp16x2': 896568832, '64/bf16x2_real': 868044032, '64/fp16x2_real': 867678208}}
 K_SCORE_TC_TRAFFIC = {"source_sha256": "", "bytes_per_pair": None}
 
 
