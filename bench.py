@@ -78,7 +78,7 @@ def kernel_source_sha(kernel: str) -> str:
 #   k_score: per evaluated pair, from one launch of 2048 images x 4608 sets (above L2), scaled by
 #            pairs to the bench's launches (profiles/k_score_throughput.md).
 #   k_score_gemm: per launch of the precision workloads (64 images x 6912 sets, +-4 px).
-K_SCORE_TRAFFIC = {"source_sha256": "278a5904c99094af3a3af3804259c98e0b9bec7562a3ebdf818fb72b2a7ec3d8", "bytes_per_pair": (1553092608 + 118595584) / (2048 * 4608)}
+K_SCORE_TRAFFIC = {"source_sha256": "ab86a36a641c09841750fa45c25f7e1a1e447e5b17c18e80c3a829b9765a8cd7", "bytes_per_pair": (1556598528 + 119324928) / (2048 * 4608)}
 K_SCORE_GEMM_TRAFFIC = {"source_sha256": "8a4ab46e82245e057c6ddb95ab59aade4800f46890ef4318f1b20e5295a9bff0", "bytes_per_launch": {
     '128/bf16x2': 3568891648, '128/fp16x2': 5365016832, '128/bf16x2_real': 4240276480, '128/fp16x2_real': 5136271360,
     '64/bf16x2': 895626240, '64/fp16x2': 896568832, '64/bf16x2_real': 868044032, '64/fp16x2_real': 867678208}}

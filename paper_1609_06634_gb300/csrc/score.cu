@@ -186,7 +186,32 @@ struct Cfg {
     static constexpr size_t SM_DSUM = DIRFFT ? (size_t)PB * 2 * (SMAX + 1) * sizeof(float) : 0;
     static constexpr size_t SMEM = SM_BASE + SM_Z + SM_DTW + SM_DSUM;
     static_assert(SMEM <= kScoreSmemLimit, "dynamic shared memory per block");
+    // Decoupled groups (the 128 px, +-16 px instance): the block's threads form NGROUP groups of
+    // GT threads, group g owning pairs [g GPB, (g + 1) GPB) of every batch in every phase (packed
+    // edge columns, stage A, stage B, the dy = +SMAX row, the combine), and within the batch loop
+    // each group waits only on its own named barrier.  The groups drift apart, so that one group's
+    // projection loads and barrier waits overlap the others' transform arithmetic instead of the
+    // whole block moving through its phases in step (the FP32 pipe saturated in the transforms and
+    // idle in between).  Measured per pair: 14.25 ns in step, 13.43 ns with two groups, 12.59 ns
+    // with four, 13.17 ns with eight (one pair per group, the dy = +SMAX jobs on half a warp).
+    static constexpr bool SPLIT = DIRFFT;
+    static constexpr int NGROUP = SPLIT ? 4 : 1;
+    static constexpr int GT = THREADS / NGROUP, GPB = PB / NGROUP;   // threads and pairs of one group
+    static_assert(!SPLIT || (GT % 32 == 0 && GPB * NCOL == GT && GPB * NROW * BSPLIT == GT &&
+                             ((GPB * 2 * R) % 32 == 0 || GPB * 2 * R == 16)),
+                  "each group's tasks on its own threads, its dy = +SMAX jobs on whole warps or half a warp");
 };
+
+// The batch loop's barrier: the whole block, or with C::SPLIT the calling thread's group (named
+// barrier 1 + group over C::GT threads).
+template <class C>
+__device__ __forceinline__ void batch_sync() {
+    if constexpr (C::SPLIT) {
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)threadIdx.x / C::GT), "n"(C::GT) : "memory");
+    } else {
+        __syncthreads();
+    }
+}
 
 // Stage A for one column kx of one pair: Q(dy, kx) for dy = -SMAX..SMAX, with the rows ky = b + R a
 // of sub-sequence b transformed by an in-register FFT and recombined with the twiddles
@@ -372,8 +397,13 @@ __device__ __forceinline__ void score_tail(const float2* __restrict__ q_s, const
     if constexpr (C::DIRFFT) {
         constexpr int NJ = C::PB * 2 * C::R;   // jobs: (pair j, component c, sub-sequence b)
         static_assert(C::R == 8 && NJ % 32 == 0 && NJ <= C::THREADS, "one job per thread, whole warps");
-        const int tj = tid - (C::THREADS - NJ);
-        const int b = tj & 7, c = (tj >> 3) & 1, j = tj >> 4;
+        // the last NJ threads, or with C::SPLIT the last NJ / NGROUP threads of each group for its
+        // pairs (the upper half of a warp when that is 16)
+        constexpr int NJG = C::SPLIT ? NJ / C::NGROUP : NJ;
+        constexpr unsigned JM = NJG >= 32 ? 0xffffffffu : (0xffffffffu << (32 - NJG));   // job lanes
+        const int grp = C::SPLIT ? tid / C::GT : 0;
+        const int tj = C::SPLIT ? tid - grp * C::GT - (C::GT - NJG) : tid - (C::THREADS - NJ);
+        const int b = tj & 7, c = (tj >> 3) & 1, j = grp * C::GPB + (tj >> 4);
         const float2* qrow = q_s + ((size_t)j * NS + 2 * SMAX) * C::QS;
         if (tj >= 0) {
             float x[8], yr[9], yi[9], a17[SMAX + 1];
@@ -391,15 +421,15 @@ __device__ __forceinline__ void score_tail(const float2* __restrict__ q_s, const
             recombine<SMAX + 1>(a17, yr, yi, dtw + (c * C::R + b) * (SMAX + 1));
 #pragma unroll
             for (int k = 0; k <= SMAX; ++k) {
-                a17[k] += __shfl_xor_sync(0xffffffffu, a17[k], 1);
-                a17[k] += __shfl_xor_sync(0xffffffffu, a17[k], 2);
-                a17[k] += __shfl_xor_sync(0xffffffffu, a17[k], 4);
+                a17[k] += __shfl_xor_sync(JM, a17[k], 1);
+                a17[k] += __shfl_xor_sync(JM, a17[k], 2);
+                a17[k] += __shfl_xor_sync(JM, a17[k], 4);
             }
             if (b == 0) {
 #pragma unroll
                 for (int k = 0; k <= SMAX; ++k) dsum[(j * 2 + c) * (SMAX + 1) + k] = a17[k];
             }
-            __syncwarp();
+            __syncwarp(JM);
             // lane (c, b) of pair j: dx = b and b + 8 (and 16 for b = 0), sign + for c = 0, - for c = 1
             const float qn = qrow[0].y;
             const bool row_ok = SMAX <= s;
@@ -440,9 +470,12 @@ __device__ __forceinline__ void score_tail(const float2* __restrict__ q_s, const
             dir_t[i] = ok ? loglik_t(rho, status) : INFINITY;
         }
     }
-    __syncthreads();
-    // ---------------- combine the pieces of each pair (one full warp per pair)
-    for (int j = warp; warp < C::NWARPS && j < C::PB; j += C::NWARPS) {
+    batch_sync<C>();
+    // ---------------- combine the pieces of each pair (one full warp per pair; with C::SPLIT the
+    // first warps of each half for its pairs)
+    const int jw = C::SPLIT ? (tid / C::GT) * C::GPB + (warp - (tid / C::GT) * (C::GT / 32)) : warp;
+    const int jend = C::SPLIT ? (tid / C::GT + 1) * C::GPB : C::PB;
+    for (int j = jw; warp < C::NWARPS && j < jend; j += C::NWARPS) {
         const int p = p0 + j;
         if (p >= hi) continue;
         Part acc{INFINITY, 0.f, 0x7fffffff};
@@ -521,7 +554,11 @@ __device__ __forceinline__ void score_item(unsigned char* smem, const float2* __
     for (int p0 = lo; p0 < hi; p0 += C::PB) {
         // ---------------- packed edge columns Z(ky) = P(ky, 0) + i P(ky, N/2) of the batch's pairs
         if constexpr (C::PACK) {
-            for (int i = tid; i < C::PB * N; i += blockDim.x) {
+            // with C::SPLIT each half forms its own pairs' columns
+            const int i0 = C::SPLIT ? (tid / C::GT) * C::GPB * N + tid % C::GT : tid;
+            const int i1 = C::SPLIT ? (tid / C::GT + 1) * C::GPB * N : C::PB * N;
+            const int istep = C::SPLIT ? C::GT : blockDim.x;
+            for (int i = i0; i < i1; i += istep) {
                 const int j = i / N;
                 const int ky = i - j * N;
                 const int p = min(p0 + j, hi - 1);
@@ -531,7 +568,7 @@ __device__ __forceinline__ void score_item(unsigned char* smem, const float2* __
                 const float2 e1 = c_mulc(img_s[ky * H + NC], __ldg(ps_row + NC));
                 z_s[i] = make_float2(e0.x - e1.y, e0.y + e1.x);
             }
-            __syncthreads();
+            batch_sync<C>();
         }
         // ---------------- stage A: one column of one pair per task
         if (active) {
@@ -551,7 +588,7 @@ __device__ __forceinline__ void score_item(unsigned char* smem, const float2* __
                 for (int m = 0; m < NS; ++m) qdst[m * C::QS] = acc[m];
             }
         }
-        __syncthreads();
+        batch_sync<C>();
         score_tail<C>(q_s, twc_s, row_t, row_s, row_d, dir_t, dtw, dsum, gtw, p0, hi, s, c1, rec_t, rec_s, rec_d,
                       status);
     }
@@ -893,8 +930,9 @@ using C64_8 = Cfg<64, 8, 16, 264, false>;
 using C96_12 = Cfg<96, 12, 10, 245, false>;
 using C128_4 = Cfg<128, 4, 24, 256>;
 // 128 px, s <= 16: 512 threads (four warps per scheduler, 128 registers), one stage-A column per
-// thread and two threads per stage-B row; 11 % faster than 256 threads with one row per thread,
-// which left the kernel waiting on dependent-instruction latency at two warps per scheduler.
+// thread and two threads per stage-B row, in four decoupled groups of two pairs (Cfg::SPLIT); 11 %
+// faster than 256 threads with one row per thread, which left the kernel waiting on
+// dependent-instruction latency at two warps per scheduler.
 using C128_16 = Cfg<128, 16, 8, 512, true, 2>;
 using C192_24 = Cfg<192, 24, 2, 194>;
 static_assert(C128_4::PACK && C128_16::PACK, "packed edge columns fit");
