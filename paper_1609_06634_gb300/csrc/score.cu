@@ -162,7 +162,10 @@ struct Cfg {
     // twiddle table twc[b][d] = W_N^(b d), d = 0..SMAX (the outputs -d use the conjugate), rows of
     // an even length TWS so that pairs (d, d + 1), d even, are read as one 16-byte load
     static constexpr int TWS = 2 * ((SMAX + 2) / 2);
-    static constexpr size_t SM_TWC = (size_t)R * TWS * sizeof(float2);
+    // the 128 px, +-16 px instance keeps a second table 2 W_N^(b d) for stage B (the weight 2 of
+    // kx != 0 rides on the twiddles, exact, instead of scaling every input)
+    static constexpr bool TW2 = N == 128 && SMAX == 16 && THREADS == 512;
+    static constexpr size_t SM_TWC = (size_t)(TW2 ? 2 : 1) * R * TWS * sizeof(float2);
     static_assert((SM_IMG + SM_QA) % 16 == 0 && (TWS * sizeof(float2)) % 16 == 0, "16-byte twiddle pairs");
     static constexpr size_t SM_ROW = (size_t)PB * NROW * BSPLIT * (2 * sizeof(float) + sizeof(int));
     static constexpr size_t SM_DIR = (size_t)NDIR * sizeof(float);
@@ -273,7 +276,9 @@ __device__ __forceinline__ void stage_a_column(float2 (&acc)[C::NS], const float
 }
 
 // Stage B for one row: rho-part(dx) = Re sum_{kx < N/2} w_kx Q(dy, kx) W_N^(kx dx), kx = b + R a;
-// only a < L/2 carries data (kx < N/2 for every b < R).
+// only a < L/2 carries data (kx < N/2 for every b < R).  With C::TW2, twc holds 2 W_N^(b d) (the
+// weight w = 2 of kx != 0) and the kx = 0 term enters halved; scaling by 2 is exact, so the sums
+// are those of the scaled inputs bit for bit.
 template <class C>
 __device__ __forceinline__ void stage_b_row(float (&acc)[C::NS], const float2* __restrict__ qrow,
                                             const float2* __restrict__ twc, int b0, int b1) {
@@ -282,8 +287,8 @@ __device__ __forceinline__ void stage_b_row(float (&acc)[C::NS], const float2* _
     for (int b = b0; b < b1; ++b) {
         float2 x[L];
 #pragma unroll
-        for (int a = 0; a < L / 2; ++a) x[a] = c_scale(qrow[b + R * a], 2.f);
-        if (b == 0) x[0] = make_float2(qrow[0].x, 0.f);   // kx = 0: weight 1, real
+        for (int a = 0; a < L / 2; ++a) x[a] = C::TW2 ? qrow[b + R * a] : c_scale(qrow[b + R * a], 2.f);
+        if (b == 0) x[0] = make_float2((C::TW2 ? 0.5f : 1.f) * qrow[0].x, 0.f);   // kx = 0: weight 1, real
         fft_dif_half_zero<L>(x);
         const float2* tw = twc + b * C::TWS;   // conjugate pairs, as in stage A
 #pragma unroll
@@ -359,7 +364,7 @@ __device__ __forceinline__ void score_tail(const float2* __restrict__ q_s, const
         float acc[NS];
 #pragma unroll
         for (int m = 0; m < NS; ++m) acc[m] = 0.f;
-        stage_b_row<C>(acc, qrow, twc_s, h * (C::R / BS), (h + 1) * (C::R / BS));
+        stage_b_row<C>(acc, qrow, twc_s + (C::TW2 ? C::R * C::TWS : 0), h * (C::R / BS), (h + 1) * (C::R / BS));
         constexpr int MH = BS == 2 ? (NS + 1) / 2 : NS;   // outputs evaluated by this thread
         int m0 = 0;
         if constexpr (BS == 2) {
@@ -516,7 +521,7 @@ __device__ __forceinline__ void score_item(unsigned char* smem, const float2* __
     float2* img_s = reinterpret_cast<float2*>(smem);
     float2* q_s = reinterpret_cast<float2*>(smem + C::SM_IMG);
     float2* twc_s = reinterpret_cast<float2*>(smem + C::SM_IMG + C::SM_QA);
-    float2* z_s = twc_s + C::R * C::TWS;   // [PB][N] packed edge columns (C::PACK)
+    float2* z_s = reinterpret_cast<float2*>(smem + C::SM_IMG + C::SM_QA + C::SM_TWC);   // [PB][N] (C::PACK)
     float* row_t = reinterpret_cast<float*>(z_s + (C::PACK ? C::PB * N : 0));
     float* row_s = row_t + C::PB * NROW * C::BSPLIT;
     int* row_d = reinterpret_cast<int*>(row_s + C::PB * NROW * C::BSPLIT);
@@ -531,7 +536,9 @@ __device__ __forceinline__ void score_item(unsigned char* smem, const float2* __
         const float2* cwN = cw_table<N>();
         for (int i = tid; i < C::R * C::TWS; i += blockDim.x) {
             const int b = i / C::TWS, d = i - (i / C::TWS) * C::TWS;
-            twc_s[i] = d <= SMAX ? cwN[pmod(b * d, N)] : make_float2(0.f, 0.f);
+            const float2 w = d <= SMAX ? cwN[pmod(b * d, N)] : make_float2(0.f, 0.f);
+            twc_s[i] = w;
+            if constexpr (C::TW2) twc_s[C::R * C::TWS + i] = make_float2(2.f * w.x, 2.f * w.y);
         }
         const float4* src = reinterpret_cast<const float4*>(img);
         float4* dst = reinterpret_cast<float4*>(img_s);

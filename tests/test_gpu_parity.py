@@ -118,6 +118,25 @@ def test_throughput_shape_subset(bioem, ctx):
     np.testing.assert_allclose(plse.cpu().numpy(), ref["pair_lse"], rtol=0, atol=TOL)
 
 
+@pytest.mark.parametrize("s", [16, 9])
+def test_throughput_pairs_ragged_ranges(bioem, ctx, s):
+    """128 px, the +-16 px kernel (pairs of a batch split between four thread groups): per-pair values
+    for ranges that leave groups with only some, or none, of their pairs inside the range (7 sets
+    from an odd offset, 3 sets, 13 sets across two batches), against the oracle."""
+    cfg = workloads.get_config("throughput")
+    wl = workloads.workload(cfg, n_img=3)
+    imgs = oracle.synthesize_images(wl)
+    quats = wl["quats"][::1024][:4]                       # 32 parameter sets
+    ref = oracle.score(imgs, wl["atoms"], quats, wl["ctfs"], cfg.sigma_A, cfg.pixel_A, s)
+    im = bioem.prepare_images(ctx, _dev(imgs), cfg.pixel_A)
+    ps = bioem.project_model(ctx, _dev(wl["atoms"]), cfg.sigma_A, _dev(quats), wl["ctfs"], cfg.npix, cfg.pixel_A)
+    for begin, count in ((5, 7), (9, 3), (17, 13), (0, 32)):
+        pmax, plse = bioem.score_pairs(ctx, im, ps, s, begin, count)
+        assert ctx.status() == 0
+        np.testing.assert_allclose(pmax.cpu().numpy(), ref["pair_max"][:, begin:begin + count], rtol=0, atol=TOL)
+        np.testing.assert_allclose(plse.cpu().numpy(), ref["pair_lse"][:, begin:begin + count], rtol=0, atol=TOL)
+
+
 @pytest.mark.parametrize("name,nq,max_shift", [("tiny", 13, 4), ("tiny", 11, 2), ("tiny", 7, 0),
                                               ("precision64", 9, 4), ("precision64", 5, 8), ("precision128", 6, 4),
                                               ("precision128", 3, 11)])
