@@ -116,12 +116,15 @@ __device__ __forceinline__ float2 c_scale(float2 a, float s) { return make_float
 // the Taylor series -(x + x^2/2 + x^3/3 + x^4/4 + x^5/5) in Horner form is used: for x <= 1/32 its
 // truncation error is below x^6/(6 (1 - x)), under 6e-9 of |t|, so the result is as accurate as the
 // rounding of its five operations allows.  Larger x take the library's log1pf.
-__device__ __forceinline__ float ln1m(float x) {
+__device__ __forceinline__ float ln1m_series(float x) {
     float p = fmaf(x, 0.2f, 0.25f);
     p = fmaf(x, p, 0.33333334f);
     p = fmaf(x, p, 0.5f);
     p = fmaf(x, p, 1.0f);
-    float t = -x * p;
+    return -x * p;
+}
+__device__ __forceinline__ float ln1m(float x) {
+    float t = ln1m_series(x);
     if (x > 0.03125f) t = log1pf(-x);
     return t;
 }

@@ -23,6 +23,7 @@
 #include <stdio.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "bioem_internal.cuh"
 #include "rdft16.cuh"
@@ -308,6 +309,16 @@ __device__ __forceinline__ void stage_b_row(float (&acc)[C::NS], const float2* _
     }
 }
 
+// 2^x by the PTX instruction ex2.approx (relative error about 2^-22; results below 2^-126 flush to
+// zero, far below the FP32 resolution of a sum that holds a term equal to 1).  The stage-B sum of
+// exp((3 - n)/2 (t - t_min)) takes it with the factor (3 - n)/2 log2(e) folded into one constant:
+// one instruction per displacement (6.5 % less k_score time than __expf at 128 px, +-16 px).
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 struct Part {
     float t;   // min ln(1 - rho^2)
     float s;   // sum exp(c1 (t(d) - t))
@@ -329,13 +340,19 @@ __device__ __forceinline__ Part merge(Part a, Part b, float c1) {
     return r;
 }
 
+// t = ln(1 - rho^2) as ln1m gives it, with |rho| >= 1 (no finite likelihood) flagged in the status
+// word and clamped; both tests sit on the rarely taken rho^2 > 1/32 branch.
 __device__ __forceinline__ float loglik_t(float rho, int* status) {
     float r2 = rho * rho;
-    if (r2 >= 1.0f) {
-        atomicOr(status, BIOEM_DEV_NUMERIC);
-        r2 = 1.0f - 5.9604645e-8f;
+    float t = ln1m_series(r2);
+    if (r2 > 0.03125f) {
+        if (r2 >= 1.0f) {
+            atomicOr(status, BIOEM_DEV_NUMERIC);
+            r2 = 1.0f - 5.9604645e-8f;
+        }
+        t = log1pf(-r2);
     }
-    return ln1m(r2);
+    return t;
 }
 
 // Stage B (row transforms), the dy = +SMAX row, the likelihood epilogue and the per-pair combine of
@@ -379,21 +396,38 @@ __device__ __forceinline__ void score_tail(const float2* __restrict__ q_s, const
         const bool row_ok = abs(r - SMAX) <= s;
         float tmin = INFINITY;
         int arg = 0x7fffffff;
-#pragma unroll
-        for (int i = 0; i < MH; ++i) {
-            const int m = m0 + i;
-            const float rho = acc[i] + (((m - SMAX) & 1) ? -qn : qn);
-            const bool ok = row_ok && m < NS && abs(m - SMAX) <= s;
-            const float t = ok ? loglik_t(rho, status) : INFINITY;
-            acc[i] = t;
-            if (t < tmin) {
-                tmin = t;
-                arg = r * NS + m;
-            }
-        }
+        // the full window (s = SMAX, uniform over the block) needs no per-output window test
+        const float qa = ((m0 - SMAX) & 1) ? -qn : qn;   // the Nyquist term of output i is (-1)^i qa
+        const float c1l = c1 * 1.44269504088896341f;
         float ssum = 0.f;
+        auto eval = [&](auto full) {
 #pragma unroll
-        for (int i = 0; i < MH; ++i) ssum += (acc[i] < INFINITY) ? __expf(c1 * (acc[i] - tmin)) : 0.f;
+            for (int i = 0; i < MH; ++i) {
+                const int m = m0 + i;
+                const float rho = acc[i] + ((i & 1) ? -qa : qa);
+                // full window: every output but the second thread's padding slot (m = NS) counts
+                const bool ok = decltype(full)::value ? (i < MH - 1 || m < NS)
+                                                      : (row_ok && m < NS && abs(m - SMAX) <= s);
+                const float t = ok ? loglik_t(rho, status) : INFINITY;
+                acc[i] = t;
+                if (t < tmin) {
+                    tmin = t;
+                    arg = r * NS + m;
+                }
+            }
+            // with the full window t_min is finite, and a left-out output's +inf gives 2^-inf = 0
+#pragma unroll
+            for (int i = 0; i < MH; ++i) {
+                if constexpr (decltype(full)::value)
+                    ssum += ex2_approx(c1l * (acc[i] - tmin));
+                else
+                    ssum += (acc[i] < INFINITY) ? ex2_approx(c1l * (acc[i] - tmin)) : 0.f;
+            }
+        };
+        if (s >= SMAX)
+            eval(std::true_type{});
+        else
+            eval(std::false_type{});
         row_t[tid] = tmin;
         row_s[tid] = ssum;
         row_d[tid] = arg;
@@ -477,7 +511,7 @@ __device__ __forceinline__ void score_tail(const float2* __restrict__ q_s, const
     }
     batch_sync<C>();
     // ---------------- combine the pieces of each pair (one full warp per pair; with C::SPLIT the
-    // first warps of each half for its pairs)
+    // first warps of each group for its pairs)
     const int jw = C::SPLIT ? (tid / C::GT) * C::GPB + (warp - (tid / C::GT) * (C::GT / 32)) : warp;
     const int jend = C::SPLIT ? (tid / C::GT + 1) * C::GPB : C::PB;
     for (int j = jw; warp < C::NWARPS && j < jend; j += C::NWARPS) {
