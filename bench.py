@@ -78,10 +78,10 @@ def kernel_source_sha(kernel: str) -> str:
 #   k_score: per evaluated pair, from one launch of 2048 images x 4608 sets (above L2), scaled by
 #            pairs to the bench's launches (profiles/k_score_throughput.md).
 #   k_score_gemm: per launch of the precision workloads (64 images x 6912 sets, +-4 px).
-K_SCORE_TRAFFIC = {"source_sha256": "ab86a36a641c09841750fa45c25f7e1a1e447e5b17c18e80c3a829b9765a8cd7", "bytes_per_pair": (1556598528 + 119324928) / (2048 * 4608)}
-K_SCORE_GEMM_TRAFFIC = {"source_sha256": "8a4ab46e82245e057c6ddb95ab59aade4800f46890ef4318f1b20e5295a9bff0", "bytes_per_launch": {
-    '128/bf16x2': 3568891648, '128/fp16x2': 5365016832, '128/bf16x2_real': 4240276480, '128/fp16x2_real': 5136271360,
-    '64/bf16x2': 895626240, '64/fp16x2': 896568832, '64/bf16x2_real': 868044032, '64/fp16x2_real': 867678208}}
+K_SCORE_TRAFFIC = {"source_sha256": "5cbad6a46143e304b29bfafe6d7c8ed5a272a6ffad62deaeba9671677c404bcc", "bytes_per_pair": (1553334016 + 118952960) / (2048 * 4608)}
+K_SCORE_GEMM_TRAFFIC = {"source_sha256": "866021ba8a409e9ba20c36deee379d976eb683b278d6152193d43b4427563f2f", "bytes_per_launch": {
+    '128/bf16x2': 3528212224, '128/fp16x2': 3795020800, '128/bf16x2_real': 3479105792, '128/fp16x2_real': 4123705344,
+    '64/bf16x2': 895100672, '64/fp16x2': 895214592, '64/bf16x2_real': 868046336, '64/fp16x2_real': 867884544}}
 K_SCORE_TC_TRAFFIC = {"source_sha256": "", "bytes_per_pair": None}
 
 
