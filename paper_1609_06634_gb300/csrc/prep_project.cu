@@ -219,9 +219,16 @@ __device__ __forceinline__ float pixel_mass(float t0, bool neg0, float t1, bool 
 template <int N>
 struct ProjCfg {
     static constexpr int CH = (2048 / N) < 8 ? 8 : (2048 / N);   // atoms per chunk (shared-memory bound)
-    static constexpr int TL = N / 16;                              // tile edge per thread
+    static constexpr int RY = N / 8;                               // rows per warp (8 warps)
+    static constexpr int CX = N / 32;                              // columns per lane
     static constexpr int NB = N + 1;                               // pixel boundaries per axis
+    static_assert(N % 32 == 0 && kThreads == 256, "8 warps x 32 lanes tile the image");
 };
+
+// |u| beyond which erfc(|u|) (about 1.4e-54 at 11) is zero in FP32: table entries past it are set
+// to zero without evaluating erfc, and an atom's rows whose two boundaries both lie past it get a
+// pixel integral of exactly zero.
+constexpr float kErfcZero = 11.f;
 
 template <int TL>
 __device__ __forceinline__ void load_row(const float* src, float (&v)[TL]) {
@@ -243,14 +250,16 @@ __device__ __forceinline__ void load_row(const float* src, float (&v)[TL]) {
     }
 }
 
-// One orientation per block.  Threads form a 16 x 16 grid, each owning a (N/16) x (N/16) pixel
-// tile.  Atoms are processed in chunks: per chunk the x and y pixel integrals are tabulated in
-// shared memory, then every thread accumulates w_a gy[a][k] gx[a][j] over the chunk.
+// One orientation per block.  Warp w owns rows [w N/8, (w + 1) N/8), lane l columns [l N/32,
+// (l + 1) N/32).  Atoms are processed in chunks: per chunk the x and y pixel integrals are tabulated
+// in shared memory (erfc evaluated only where it is not zero in FP32), then every thread accumulates
+// w_a gy[a][k] gx[a][j] over the chunk, a warp skipping the atoms whose y integrals vanish on all of
+// its rows (their products are exact zeros, so the sums are unchanged bit for bit).
 template <int N>
 __global__ void __launch_bounds__(kThreads) k_project(const float4* __restrict__ atoms, int n_atoms,
                                                        const float4* __restrict__ quats, double sigma,
                                                        double pixel, float* __restrict__ out) {
-    constexpr int CH = ProjCfg<N>::CH, TL = ProjCfg<N>::TL, NB = ProjCfg<N>::NB;
+    constexpr int CH = ProjCfg<N>::CH, RY = ProjCfg<N>::RY, CX = ProjCfg<N>::CX, NB = ProjCfg<N>::NB;
     __shared__ double rot[6];
     __shared__ float bx_t[CH][NB], by_t[CH][NB];
     __shared__ __align__(16) float gx[CH][N];
@@ -260,6 +269,7 @@ __global__ void __launch_bounds__(kThreads) k_project(const float4* __restrict__
     // of a float64 evaluation of u rounded to float
     __shared__ float axh[CH], axl[CH], ayh[CH], ayl[CH];
     __shared__ float aw[CH];
+    __shared__ int rlo[CH], rhi[CH];   // rows outside [rlo, rhi] have a zero y integral for the atom
 
     const int q = blockIdx.x;
     if (threadIdx.x == 0) {
@@ -271,15 +281,16 @@ __global__ void __launch_bounds__(kThreads) k_project(const float4* __restrict__
         rot[3] = 2.0 * (x * y + w * z); rot[4] = 1.0 - 2.0 * (x * x + z * z); rot[5] = 2.0 * (y * z - w * x);
     }
     __syncthreads();
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    float acc[TL][TL];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;   // rows [warp RY, +RY), columns [lane CX, +CX)
+    float acc[RY][CX];
 #pragma unroll
-    for (int i = 0; i < TL; ++i)
+    for (int i = 0; i < RY; ++i)
 #pragma unroll
-        for (int j = 0; j < TL; ++j) acc[i][j] = 0.f;
+        for (int j = 0; j < CX; ++j) acc[i][j] = 0.f;
     const double inv = 1.0 / (sigma * 1.4142135623730951);
     const double dd = pixel * inv;                 // D: the pixel in units of sigma sqrt 2
     const float d_hi = (float)dd, d_lo = (float)(dd - (double)d_hi);
+    const float inv_d = (float)(1.0 / dd);        // for the rows an atom can reach (margins absorb rounding)
     const double a_off = (0.5 * N + 0.5) * pixel;  // edge_j = j pixel - a_off
 
     for (int a0 = 0; a0 < n_atoms; a0 += CH) {
@@ -294,8 +305,13 @@ __global__ void __launch_bounds__(kThreads) k_project(const float4* __restrict__
                 ayh[a] = (float)ay;
                 ayl[a] = (float)(ay - (double)ayh[a]);
                 aw[a] = p.w;
+                // boundary j has |u_j| < kErfcZero for (A - 11) / D < j < (A + 11) / D; row j uses
+                // boundaries j and j + 1 (one row of margin each side for rounding)
+                rlo[a] = (int)floorf(((float)ay - kErfcZero) * inv_d) - 2;
+                rhi[a] = (int)ceilf(((float)ay + kErfcZero) * inv_d) + 1;
             } else {
                 axh[a] = 1.0e30f; axl[a] = 0.f; ayh[a] = 1.0e30f; ayl[a] = 0.f; aw[a] = 0.f;
+                rlo[a] = 1 << 30; rhi[a] = -(1 << 30);
             }
         }
         __syncthreads();
@@ -305,7 +321,9 @@ __global__ void __launch_bounds__(kThreads) k_project(const float4* __restrict__
             const float fj = (float)j;
             const float ux = fmaf(fj, d_hi, -axh[a]) + fmaf(fj, d_lo, -axl[a]);
             const float uy = fmaf(fj, d_hi, -ayh[a]) + fmaf(fj, d_lo, -ayl[a]);
-            const float ex = erfcf(fabsf(ux)), ey = erfcf(fabsf(uy));
+            float ex = 0.f, ey = 0.f;
+            if (fabsf(ux) < kErfcZero) ex = erfcf(fabsf(ux));
+            if (fabsf(uy) < kErfcZero) ey = erfcf(fabsf(uy));
             // the sign bit carries the sign of u, also when erfc underflows to zero
             bx_t[a][j] = __int_as_float(__float_as_int(ex) | (ux < 0.f ? (int)0x80000000 : 0));
             by_t[a][j] = __int_as_float(__float_as_int(ey) | (uy < 0.f ? (int)0x80000000 : 0));
@@ -320,21 +338,23 @@ __global__ void __launch_bounds__(kThreads) k_project(const float4* __restrict__
         }
         __syncthreads();
         for (int a = 0; a < na; ++a) {
-            float vy[TL], vx[TL];
-            load_row<TL>(&gy[a][ty * TL], vy);
-            load_row<TL>(&gx[a][tx * TL], vx);
+            // the warp's rows all have a zero integral for this atom: its products are all +0
+            if (rhi[a] < warp * RY || rlo[a] >= (warp + 1) * RY) continue;
+            float vy[RY], vx[CX];
+            load_row<RY>(&gy[a][warp * RY], vy);
+            load_row<CX>(&gx[a][lane * CX], vx);
 #pragma unroll
-            for (int i = 0; i < TL; ++i)
+            for (int i = 0; i < RY; ++i)
 #pragma unroll
-                for (int j = 0; j < TL; ++j) acc[i][j] = fmaf(vy[i], vx[j], acc[i][j]);
+                for (int j = 0; j < CX; ++j) acc[i][j] = fmaf(vy[i], vx[j], acc[i][j]);
         }
         __syncthreads();
     }
     float* o = out + (size_t)q * N * N;
 #pragma unroll
-    for (int i = 0; i < TL; ++i)
+    for (int i = 0; i < RY; ++i)
 #pragma unroll
-        for (int j = 0; j < TL; ++j) o[(ty * TL + i) * N + tx * TL + j] = acc[i][j];
+        for (int j = 0; j < CX; ++j) o[(warp * RY + i) * N + lane * CX + j] = acc[i][j];
 }
 
 // T[c][ky][kx] = CTF(s) Env(s) for PSF c on the half-spectrum grid, evaluated in float64.
