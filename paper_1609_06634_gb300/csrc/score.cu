@@ -595,7 +595,7 @@ __device__ __forceinline__ void score_item(unsigned char* smem, const float2* __
     for (int p0 = lo; p0 < hi; p0 += C::PB) {
         // ---------------- packed edge columns Z(ky) = P(ky, 0) + i P(ky, N/2) of the batch's pairs
         if constexpr (C::PACK) {
-            // with C::SPLIT each half forms its own pairs' columns
+            // with C::SPLIT each group forms its own pairs' columns
             const int i0 = C::SPLIT ? (tid / C::GT) * C::GPB * N + tid % C::GT : tid;
             const int i1 = C::SPLIT ? (tid / C::GT + 1) * C::GPB * N : C::PB * N;
             const int istep = C::SPLIT ? C::GT : blockDim.x;

@@ -48,6 +48,14 @@ def test_every_global_name_in_bench_is_defined():
     assert not missing, missing
 
 
+def test_kernel_identity_ignores_comments_only():
+    """A stored DRAM figure stays attached to a kernel while only its comments change."""
+    bench = _bench()
+    code = "a = b; // note\n/* block\n comment */ c = d;   \n\n"
+    assert bench._code_only(code) == bench._code_only("a = b;\n c = d;")
+    assert bench._code_only(code) != bench._code_only("a = b;\n c = e;")
+
+
 def test_traffic_tables_and_work_per_eval():
     bench = _bench()
     # a stored figure names the kernel source it was taken on ("" until one is taken)
