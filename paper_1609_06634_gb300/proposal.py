@@ -9,6 +9,7 @@ offsets and noise.
 """
 from __future__ import annotations
 
+import concurrent.futures
 import math
 import time
 
@@ -99,21 +100,62 @@ def train_redrawn(ctx: Context, net: CNN, atoms_dev: list, d: dict, cfg, epochs:
     return losses
 
 
-def _cell_lists(bins: np.ndarray, pos: np.ndarray, n_defocus: int, n_b: int, kids: int):
+def _cell_lists(bins: np.ndarray, pos: np.ndarray, n_defocus: int, n_b: int, kids: int, cells=None):
     """Per-image parameter-set lists (CSR) of the joint bins whose cells are in the current wave:
     bin (cell, defocus d) -> sets ((pos[cell] * kids + j) * n_ctf + d * n_b + b) for its kids child
     orientations j and every B index b, in image-major, bin-major order.  Returns (mask [n, K] of
-    the bins in this wave, offsets [n + 1], flat set indices)."""
-    cells, dd = bins // n_defocus, bins % n_defocus
+    the bins in this wave, offsets [n + 1] int64, flat set indices int32).  `cells` = bins //
+    n_defocus may be passed in when the same bins are listed for many waves."""
+    bins = np.asarray(bins)
+    if cells is None:
+        cells = bins // n_defocus
     pc = pos[cells]
     mask = pc >= 0
     nctf = n_defocus * n_b
-    sel_p, sel_d = pc[mask], dd[mask]                                               # row-major: by image
-    base = (sel_p * kids)[:, None] + np.arange(kids)[None, :]                       # [n_sel, kids]
-    flat = ((base * nctf + (sel_d * n_b)[:, None])[:, :, None] + np.arange(n_b)).reshape(-1)
-    counts = mask.sum(axis=1) * kids * n_b
-    off = np.concatenate([[0], np.cumsum(counts)])
+    # set index = pos * kids * nctf + d * n_b  +  (j * nctf + b): one int32 head per selected bin plus
+    # the bin's kids * n_b fixed offsets, built by one broadcast add
+    head = (pc[mask].astype(np.int32) * np.int32(kids * nctf)
+            + (bins[mask] % n_defocus).astype(np.int32) * np.int32(n_b))
+    tail = (np.arange(kids, dtype=np.int32)[:, None] * np.int32(nctf)
+            + np.arange(n_b, dtype=np.int32)[None, :]).reshape(-1)
+    flat = (head[:, None] + tail[None, :]).reshape(-1)
+    counts = mask.sum(axis=1).astype(np.int64) * (kids * n_b)
+    off = np.zeros(len(counts) + 1, dtype=np.int64)
+    np.cumsum(counts, out=off[1:])
     return mask, off, flat
+
+
+def _wave_lists(bins: np.ndarray, n_coarse: int, n_defocus: int, n_b: int, kids: int, wave: int):
+    """The lists of _cell_lists for every wave of the used cells (sorted cell ids, `wave` cells per
+    wave), without a pass over all bins per wave: the bins are grouped by wave once (a stable radix
+    sort of their wave numbers keeps each wave's bins in image-major, bin-major order), then each
+    wave's lists are built from its own bins only.  Yields (cells of the wave, flattened indices
+    into bins of the wave's bins, offsets [n + 1] int64, flat set indices int32)."""
+    bins = np.asarray(bins)
+    n, K = bins.shape
+    cells = (bins // n_defocus).ravel()
+    used = np.unique(cells)
+    rank = np.full(n_coarse, -1, dtype=np.int64)
+    rank[used] = np.arange(len(used))
+    r = rank[cells]
+    n_waves = (len(used) + wave - 1) // wave
+    w = (r // wave).astype(np.int16 if n_waves < 32768 else np.int32)
+    order = np.argsort(w, kind="stable")
+    bounds = np.zeros(n_waves + 1, dtype=np.int64)
+    np.cumsum(np.bincount(w, minlength=n_waves), out=bounds[1:])
+    nctf = n_defocus * n_b
+    tail = (np.arange(kids, dtype=np.int32)[:, None] * np.int32(nctf)
+            + np.arange(n_b, dtype=np.int32)[None, :]).reshape(-1)
+    flat_bins = bins.ravel()
+    for t in range(n_waves):
+        idx = order[bounds[t]:bounds[t + 1]]
+        pos = (r[idx] - t * wave).astype(np.int32)
+        head = pos * np.int32(kids * nctf) + (flat_bins[idx] % n_defocus).astype(np.int32) * np.int32(n_b)
+        flat = (head[:, None] + tail[None, :]).reshape(-1)
+        counts = np.bincount(idx // K, minlength=n).astype(np.int64) * (kids * n_b)
+        off = np.zeros(n + 1, dtype=np.int64)
+        np.cumsum(counts, out=off[1:])
+        yield used[t * wave:(t + 1) * wave], idx, off, flat
 
 
 def score_cells(ctx: Context, images, atoms_dev, bins: np.ndarray, cfg, wave: int = 256) -> dict:
@@ -132,39 +174,39 @@ def score_cells(ctx: Context, images, atoms_dev, bins: np.ndarray, cfg, wave: in
     S = (2 * cfg.max_shift + 1) ** 2
     log_norm = math.log(len(fine_q) * nctf * S)
     bins = np.asarray(bins, dtype=np.int64)
-    used = np.unique(bins // nd)
+    n_cells = 0
     acc = torch.empty((n_img, 2), dtype=torch.float64, device=dev)
     first = True
     evals = 0
     t0 = time.perf_counter()
     rows = cfg.ctf_rows()
-    for w0 in range(0, len(used), wave):
-        wc = used[w0:w0 + wave]
-        pos = np.full(cfg.n_coarse, -1, dtype=np.int64)
-        pos[wc] = np.arange(len(wc))
+    for wc, _, off, flat in _wave_lists(bins, cfg.n_coarse, nd, nb, kids, wave):
+        n_cells += len(wc)
         child = workloads.hopf_children(cfg.coarse_level, cfg.fine_level, wc).ravel()
         q = torch.from_numpy(np.ascontiguousarray(fine_q[child])).to(dev)
         ps = project_model(ctx, atoms_dev, cfg.sigma_A, q, rows, cfg.npix, cfg.pixel_A)
-        _, off, flat = _cell_lists(bins, pos, nd, nb, kids)
         counts = np.diff(off)
         evals += int(counts.sum())
         score_gathered(ctx, images, ps, cfg.max_shift, torch.from_numpy(off.astype(np.int32)).to(dev),
-                       torch.from_numpy(flat.astype(np.int32)).to(dev), max(1, int(counts.max())), acc, first)
+                       torch.from_numpy(flat).to(dev), max(1, int(counts.max())), acc, first)
         first = False
         ps.close()
     logp = acc_logP(ctx, acc, log_norm)
     torch.cuda.synchronize()
     return {"logP": logp.cpu().numpy(), "evals": evals, "seconds": time.perf_counter() - t0,
-            "cells": int(len(used))}
+            "cells": int(n_cells)}
 
 
-def rerank_coarse(ctx: Context, images, atoms_dev, bins: np.ndarray, cfg, keep: int, wave: int = 2304,
+def rerank_coarse(ctx: Context, images, atoms_dev, bins: np.ndarray, cfg, keep: int, wave: int = 128,
                   level: int | None = None) -> dict:
     """Exact re-ranking of proposed joint bins: bin (coarse cell, defocus) is scored at the cell's
     orientations of Hopf level `level` (default: the coarse level itself, one orientation per cell;
     one level finer: the cell's 8 children) x its defocus x every B, as ln sum over them and over the
     displacements of L (the closed-form likelihood of the scoring path, summed by the library); per
-    image the `keep` best bins are returned, best first.  The cells are projected in waves."""
+    image the `keep` best bins are returned, best first.  The cells are projected in waves of `wave`
+    orientations: 128 x 8 PSFs = 68 MB of projection spectra stay in L2 while every image scores its
+    share of them (K1 = 8192 at level 3, 2000 images: 4.5e7 evals/s against 3.5e7 with waves of
+    2304 orientations; 32 orientations per wave lose more to per-wave launches than they gain)."""
     import workloads
     torch = _torch()
     dev = ctx.device
@@ -174,25 +216,30 @@ def rerank_coarse(ctx: Context, images, atoms_dev, bins: np.ndarray, cfg, keep: 
     grid_q = workloads.hopf_grid(level).astype(np.float32)
     bins = np.asarray(bins, dtype=np.int64)
     scores = np.full(bins.shape, -np.inf)
-    used = np.unique(bins // nd)
-    wave = max(1, wave // kids)
+    flat_scores = scores.reshape(-1)
     evals = 0
     t0 = time.perf_counter()
-    for w0 in range(0, len(used), wave):
-        wc = used[w0:w0 + wave]
-        pos = np.full(cfg.n_coarse, -1, dtype=np.int64)
-        pos[wc] = np.arange(len(wc))
-        child = workloads.hopf_children(cfg.coarse_level, level, wc).ravel() if kids > 1 else wc
-        ps = project_model(ctx, atoms_dev, cfg.sigma_A, torch.from_numpy(np.ascontiguousarray(grid_q[child])).to(dev),
-                           cfg.ctf_rows(), cfg.npix, cfg.pixel_A)
-        mask, off, flat = _cell_lists(bins, pos, nd, nb, kids)
-        counts = np.diff(off)
-        v = score_gathered_pairs(ctx, images, ps, cfg.max_shift, torch.from_numpy(off.astype(np.int32)).to(dev),
-                                 torch.from_numpy(flat.astype(np.int32)).to(dev), max(1, int(counts.max())))
-        # ln sum over each bin's children and B-factors (the library's log-sum-exp; the host orders bins)
-        scores[mask] = group_logsumexp(ctx, v, kids * nb).cpu().numpy()
-        evals += int(counts.sum())
-        ps.close()
+    # the host builds the next wave's lists while the GPU scores the current one
+    gen = _wave_lists(bins, cfg.n_coarse, nd, nb, kids, max(1, wave // kids))
+    with concurrent.futures.ThreadPoolExecutor(max_workers=1) as pool:
+        pending = pool.submit(next, gen, None)
+        while True:
+            item = pending.result()
+            if item is None:
+                break
+            pending = pool.submit(next, gen, None)
+            wc, idx, off, flat = item
+            child = workloads.hopf_children(cfg.coarse_level, level, wc).ravel() if kids > 1 else wc
+            ps = project_model(ctx, atoms_dev, cfg.sigma_A,
+                               torch.from_numpy(np.ascontiguousarray(grid_q[child])).to(dev), cfg.ctf_rows(),
+                               cfg.npix, cfg.pixel_A)
+            counts = np.diff(off)
+            v = score_gathered_pairs(ctx, images, ps, cfg.max_shift, torch.from_numpy(off.astype(np.int32)).to(dev),
+                                     torch.from_numpy(flat).to(dev), max(1, int(counts.max())))
+            # ln sum over each bin's children and B-factors (the library's log-sum-exp; the host orders bins)
+            flat_scores[idx] = group_logsumexp(ctx, v, kids * nb).cpu().numpy()
+            evals += int(counts.sum())
+            ps.close()
     order = np.argsort(-scores, axis=1, kind="stable")[:, :keep]
     return {"bins": np.take_along_axis(bins, order, axis=1), "evals": evals,
             "seconds": time.perf_counter() - t0}

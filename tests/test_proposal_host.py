@@ -28,3 +28,21 @@ def test_cell_lists_match_a_per_image_loop():
         counts.append(len(row))
     np.testing.assert_array_equal(flat, want)
     np.testing.assert_array_equal(off, np.concatenate([[0], np.cumsum(counts)]))
+
+
+def test_wave_lists_match_cell_lists():
+    """The once-sorted per-wave lists equal _cell_lists' per-wave pass over all bins."""
+    rng = np.random.default_rng(9)
+    n_coarse, nd, nb, kids, wave = 60, 4, 2, 8, 7
+    bins = np.stack([rng.choice(n_coarse * nd, 11, replace=False) for _ in range(9)])
+    used = np.unique(bins // nd)
+    waves = list(proposal._wave_lists(bins, n_coarse, nd, nb, kids, wave))
+    assert len(waves) == -(-len(used) // wave)
+    for t, (wc, idx, off, flat) in enumerate(waves):
+        np.testing.assert_array_equal(wc, used[t * wave:(t + 1) * wave])
+        pos = np.full(n_coarse, -1)
+        pos[wc] = np.arange(len(wc))
+        mask, off_ref, flat_ref = proposal._cell_lists(bins, pos, nd, nb, kids)
+        np.testing.assert_array_equal(idx, np.flatnonzero(mask.ravel()))
+        np.testing.assert_array_equal(off, off_ref)
+        np.testing.assert_array_equal(flat, flat_ref)
