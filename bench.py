@@ -465,6 +465,8 @@ def bench_ours(args):
                                f"on this GPU in this run, median SM clock {peaks['sm_mhz']} MHz during it"),
                 "peak_nominal": nominal,
                 "peak_nominal_basis": f"{props.multi_processor_count} SMs x 128 lanes x 2 flop x {peak_mhz:.0f} MHz",
+                "fp32_ffma_measured_tflops": peaks["fp32_ffma_tflops"],
+                "fp32_ffma2_measured_tflops": peaks["fp32_ffma2_tflops"],
                 "fp64_peak_measured_tflops": peaks["fp64_tflops"],
                 "flops_per_eval": fpe, "kernel_ms_per_step": k_ms / args.steps, "launches_per_step": k_n / args.steps}
         if clk and clk.get("sm_mhz") and peaks.get("sm_mhz"):
